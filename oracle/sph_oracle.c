@@ -1,0 +1,547 @@
+/*
+ * sph_oracle.c -- plain FP64 CPU oracle for the SPH density / smoothing-length solve.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The CUDA library never links, loads or calls this file.
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg use it.
+ * It shares no code, header, table or constant generator with the CUDA path.
+ *
+ * What it computes (Baruffa et al., "Performance Optimisation of SPH Algorithms for
+ * Multi/Many-Core Architectures", arXiv:1612.06090):
+ *
+ *  - Density by kernel interpolation, Eq. (1): rho_i = sum_j m_j W(|r_i - r_j|, h).
+ *    Read in gather form: the smoothing length of the target particle i is used for
+ *    every pair (the printed equation carries h_j; see the readings list).
+ *    The self pair j = i is included.  A neighbour is a particle with r_ij < h, strictly.
+ *  - Kernel W: M4 cubic spline in 3-D with compact support h,
+ *    W(r, h) = 8 / (pi h^3) w(q), q = r / h,
+ *    w = 1 - 6 q^2 + 6 q^3 (q <= 1/2), 2 (1 - q)^3 (1/2 < q < 1), 0 otherwise.
+ *    (The paper runs a Wendland C6 kernel with 295 neighbours, Sec. II-B; this solve
+ *    uses the M4 kernel with a target of Nngb weighted neighbours.)
+ *  - Weighted neighbour count N_w(h) = (4 pi / 3) h^3 sum_j W(r_ij, h) = (32/3) sum_j w(q_j)
+ *    and its derivative dN_w/dh = (32/3)(1/h) sum_j (-q_j w'(q_j)).
+ *  - The iteration of Sec. IV-A (Listings 2 and 3): particles whose neighbour count is
+ *    off target get a new h and are recomputed; each pass runs only over the "todo"
+ *    list of still-unconverged particles, spread over OpenMP threads with dynamic
+ *    scheduling (the "lockless" scheme).  The paper gives no h-update rule; this one is:
+ *      converged      iff |N_w - Nngb| <= tol (outputs come from that same evaluation);
+ *      bracket        N_w < Nngb -> h_lo = h, else h_hi = h;
+ *      Newton         h' = h - (N_w - Nngb) / N_w', accepted iff N_w' > 0,
+ *                     h_lo < h' < h_hi and h/2 <= h' <= 2h;
+ *      fallback       both bounds set -> (h_lo + h_hi) / 2; only h_lo -> h * 2^(1/3);
+ *                     only h_hi -> h / 2^(1/3) (the double literal 1.2599210498948732);
+ *      box limit      periodic and h' >= min(box) / 2 -> the particle stops with
+ *                     status "h exceeds box";
+ *      pass limit     after max_iter evaluations -> status "not converged".
+ *    An unconverged particle reports the last h it was evaluated at, with the density
+ *    and counts of that evaluation.
+ *
+ * Neighbour search: a stack of uniform FP64 bucket grids (cell size box / 2^k).  For a
+ * target with smoothing length h the grid with the coarsest cells no larger than h is
+ * used and every bucket meeting [x - h, x + h] is scanned.  Buckets are row-major cell
+ * ids sorted with qsort and looked up with binary search.  A brute-force O(N) scan per
+ * target is also provided; the two are cross-checked by the tests.
+ *
+ * Build with -ffp-contract=off so that every product and sum rounds separately.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_MAX_LEVEL 20 /* 2^60 cell ids still fit an int64 */
+#define ORACLE_MAX_PASSES 64
+#define ORACLE_GROWTH 1.2599210498948732 /* 2^(1/3) as the double literal of the readings */
+
+enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_EXCEEDS_BOX = 2 };
+
+/* ------------------------------------------------------------------------------------ */
+/* Kernel                                                                                */
+/* ------------------------------------------------------------------------------------ */
+
+/* Dimensionless M4 shape w(q); W = 8/(pi h^3) w(q). */
+double oracle_w(double q)
+{
+    if (q <= 0.5) {
+        double t = 6.0 * q - 6.0;
+        return 1.0 + (q * q) * t;
+    }
+    if (q < 1.0) {
+        double a = 1.0 - q;
+        return 2.0 * (a * a * a);
+    }
+    return 0.0;
+}
+
+/* -q w'(q), the term whose sum gives dN_w/dh. */
+double oracle_mqdw(double q)
+{
+    if (q <= 0.5) {
+        return (q * q) * (12.0 - 18.0 * q);
+    }
+    if (q < 1.0) {
+        double a = 1.0 - q;
+        return (6.0 * q) * (a * a);
+    }
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Particle set and bucket grids                                                         */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t n;
+    const double *x, *y, *z, *m;
+    int periodic;
+    double box[3];    /* periodic box lengths */
+    double origin[3]; /* non-periodic: bounding-box minimum */
+    double ext[3];    /* periodic: box; non-periodic: one cubic extent for all three */
+} pset;
+
+typedef struct {
+    int built;
+    int64_t g;        /* cells per dimension, 2^level */
+    double cell[3];   /* cell size per dimension */
+    int64_t *ids;     /* sorted cell ids */
+    int64_t *order;   /* particle index for each sorted entry */
+} bucket_grid;
+
+typedef struct {
+    int64_t id, idx;
+} id_idx;
+
+static int cmp_id_idx(const void *a, const void *b)
+{
+    const id_idx *p = (const id_idx *)a, *q = (const id_idx *)b;
+    if (p->id < q->id) return -1;
+    if (p->id > q->id) return 1;
+    if (p->idx < q->idx) return -1;
+    if (p->idx > q->idx) return 1;
+    return 0;
+}
+
+static int64_t cell_coord(double x, double origin, double cell, int64_t g)
+{
+    double f = floor((x - origin) / cell);
+    if (f < 0.0) return 0;
+    if (f > (double)(g - 1)) return g - 1;
+    return (int64_t)f;
+}
+
+static int build_grid(const pset *ps, int level, bucket_grid *bg)
+{
+    int64_t n = ps->n, g = (int64_t)1 << level;
+    bg->g = g;
+    for (int d = 0; d < 3; d++) bg->cell[d] = ps->ext[d] / (double)g;
+    id_idx *tmp = (id_idx *)malloc((size_t)(n > 0 ? n : 1) * sizeof(id_idx));
+    bg->ids = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    bg->order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!tmp || !bg->ids || !bg->order) {
+        free(tmp);
+        free(bg->ids);
+        free(bg->order);
+        bg->ids = bg->order = NULL;
+        return -1;
+    }
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t ix = cell_coord(ps->x[i], ps->origin[0], bg->cell[0], g);
+        int64_t iy = cell_coord(ps->y[i], ps->origin[1], bg->cell[1], g);
+        int64_t iz = cell_coord(ps->z[i], ps->origin[2], bg->cell[2], g);
+        tmp[i].id = ix + g * (iy + g * iz);
+        tmp[i].idx = i;
+    }
+    qsort(tmp, (size_t)n, sizeof(id_idx), cmp_id_idx);
+    for (int64_t i = 0; i < n; i++) {
+        bg->ids[i] = tmp[i].id;
+        bg->order[i] = tmp[i].idx;
+    }
+    free(tmp);
+    bg->built = 1;
+    return 0;
+}
+
+static void free_grid(bucket_grid *bg)
+{
+    free(bg->ids);
+    free(bg->order);
+    memset(bg, 0, sizeof(*bg));
+}
+
+/* First sorted position whose id is >= key. */
+static int64_t lower_bound_id(const int64_t *ids, int64_t n, int64_t key)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (ids[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/* Coarsest grid level whose cells are no larger than h in every dimension. */
+static int level_for(const pset *ps, double h)
+{
+    double emax = ps->ext[0];
+    if (ps->ext[1] > emax) emax = ps->ext[1];
+    if (ps->ext[2] > emax) emax = ps->ext[2];
+    int k = 0;
+    while (k < ORACLE_MAX_LEVEL && emax / (double)((int64_t)1 << k) > h) k++;
+    return k;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* One density evaluation at fixed h                                                     */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    double sum_mw, sum_w, sum_dw; /* sum m_j w_j, sum w_j, sum -q_j w'(q_j) */
+    int64_t count;                /* #{j : r_ij < h} */
+    int64_t near;                 /* #{j : |r_ij - h| <= near_rel * h} */
+} acc_t;
+
+static inline double min_image(double dx, double L)
+{
+    if (dx > 0.5 * L) return dx - L;
+    if (dx < -0.5 * L) return dx + L;
+    return dx;
+}
+
+static inline void pair(const pset *ps, int64_t i, int64_t j, double h, double h2,
+                        double near_rel, acc_t *a)
+{
+    double dx = ps->x[j] - ps->x[i];
+    double dy = ps->y[j] - ps->y[i];
+    double dz = ps->z[j] - ps->z[i];
+    if (ps->periodic) {
+        dx = min_image(dx, ps->box[0]);
+        dy = min_image(dy, ps->box[1]);
+        dz = min_image(dz, ps->box[2]);
+    }
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (near_rel > 0.0) {
+        double r = sqrt(r2);
+        if (fabs(r - h) <= near_rel * h) a->near++;
+    }
+    if (r2 < h2) {
+        double r = sqrt(r2);
+        double q = r / h;
+        double w = oracle_w(q);
+        a->sum_mw += ps->m[j] * w;
+        a->sum_w += w;
+        a->sum_dw += oracle_mqdw(q);
+        a->count++;
+    }
+}
+
+static void eval_brute(const pset *ps, int64_t i, double h, double near_rel, acc_t *a)
+{
+    double h2 = h * h;
+    memset(a, 0, sizeof(*a));
+    for (int64_t j = 0; j < ps->n; j++) pair(ps, i, j, h, h2, near_rel, a);
+}
+
+/* Scan every bucket meeting [x_i - h, x_i + h] in each dimension. */
+static void eval_grid(const pset *ps, const bucket_grid *bg, int64_t i, double h,
+                      double near_rel, acc_t *a)
+{
+    double h2 = h * h;
+    const double xi[3] = {ps->x[i], ps->y[i], ps->z[i]};
+    int64_t lo[3], cnt[3];
+    int64_t g = bg->g;
+    memset(a, 0, sizeof(*a));
+    for (int d = 0; d < 3; d++) {
+        double c = bg->cell[d];
+        int64_t a0 = (int64_t)floor((xi[d] - h - ps->origin[d]) / c);
+        int64_t a1 = (int64_t)floor((xi[d] + h - ps->origin[d]) / c);
+        if (ps->periodic) {
+            if (a1 - a0 + 1 >= g) { /* the whole periodic row, each bucket once */
+                lo[d] = 0;
+                cnt[d] = g;
+            } else {
+                lo[d] = a0;
+                cnt[d] = a1 - a0 + 1;
+            }
+        } else {
+            if (a0 < 0) a0 = 0;
+            if (a1 > g - 1) a1 = g - 1;
+            lo[d] = a0;
+            cnt[d] = a1 >= a0 ? a1 - a0 + 1 : 0;
+        }
+    }
+    for (int64_t kz = 0; kz < cnt[2]; kz++) {
+        int64_t cz = lo[2] + kz;
+        if (ps->periodic) cz = ((cz % g) + g) % g;
+        for (int64_t ky = 0; ky < cnt[1]; ky++) {
+            int64_t cy = lo[1] + ky;
+            if (ps->periodic) cy = ((cy % g) + g) % g;
+            for (int64_t kx = 0; kx < cnt[0]; kx++) {
+                int64_t cx = lo[0] + kx;
+                if (ps->periodic) cx = ((cx % g) + g) % g;
+                int64_t id = cx + g * (cy + g * cz);
+                int64_t s = lower_bound_id(bg->ids, ps->n, id);
+                for (int64_t p = s; p < ps->n && bg->ids[p] == id; p++)
+                    pair(ps, i, bg->order[p], h, h2, near_rel, a);
+            }
+        }
+    }
+}
+
+static void finish(double h, const acc_t *a, double *rho, double *nw, double *dnw)
+{
+    const double pi = 3.14159265358979323846;
+    *rho = a->sum_mw * (8.0 / (pi * h * h * h));
+    *nw = (32.0 / 3.0) * a->sum_w;
+    *dnw = (32.0 / 3.0) * a->sum_dw / h;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Particle-set setup                                                                    */
+/* ------------------------------------------------------------------------------------ */
+
+static void setup_pset(pset *ps, int64_t n, const double *x, const double *y, const double *z,
+                       const double *m, const double *box, int periodic)
+{
+    memset(ps, 0, sizeof(*ps));
+    ps->n = n;
+    ps->x = x;
+    ps->y = y;
+    ps->z = z;
+    ps->m = m;
+    ps->periodic = periodic;
+    if (periodic) {
+        for (int d = 0; d < 3; d++) {
+            ps->box[d] = box[d];
+            ps->origin[d] = 0.0;
+            ps->ext[d] = box[d];
+        }
+    } else {
+        double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+        const double *c[3] = {x, y, z};
+        for (int64_t i = 0; i < n; i++)
+            for (int d = 0; d < 3; d++) {
+                if (c[d][i] < lo[d]) lo[d] = c[d][i];
+                if (c[d][i] > hi[d]) hi[d] = c[d][i];
+            }
+        double e = 0.0;
+        for (int d = 0; d < 3; d++)
+            if (n > 0 && hi[d] - lo[d] > e) e = hi[d] - lo[d];
+        if (e <= 0.0) e = 1.0;
+        e *= 1.0000001; /* keep the maximum inside the last bucket */
+        for (int d = 0; d < 3; d++) {
+            ps->origin[d] = n > 0 ? lo[d] : 0.0;
+            ps->ext[d] = e;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Public entry points                                                                   */
+/* ------------------------------------------------------------------------------------ */
+
+/* Fixed-h evaluation for the targets listed in `targets` (NULL: all particles).
+ * Outputs are indexed by target position.  mode 0 = bucket grids, 1 = brute force.
+ * near_rel > 0 also counts pairs with |r - h| <= near_rel * h into near_out. */
+int oracle_eval(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                const double *box, int periodic, int64_t n_targets, const int64_t *targets,
+                const double *h, int mode, double near_rel, double *rho, double *nw, double *dnw,
+                int64_t *count, int64_t *near_out)
+{
+    pset ps;
+    setup_pset(&ps, n, x, y, z, m, box, periodic);
+    if (n_targets < 0) n_targets = n;
+    bucket_grid grids[ORACLE_MAX_LEVEL + 1];
+    memset(grids, 0, sizeof(grids));
+    if (mode == 0) {
+        for (int64_t t = 0; t < n_targets; t++) {
+            int k = level_for(&ps, h[t]);
+            if (!grids[k].built && build_grid(&ps, k, &grids[k]) != 0) return -1;
+        }
+    }
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_targets; t++) {
+        int64_t i = targets ? targets[t] : t;
+        acc_t a;
+        if (mode == 0) eval_grid(&ps, &grids[level_for(&ps, h[t])], i, h[t], near_rel, &a);
+        else eval_brute(&ps, i, h[t], near_rel, &a);
+        finish(h[t], &a, &rho[t], &nw[t], &dnw[t]);
+        count[t] = a.count;
+        if (near_out) near_out[t] = a.near;
+    }
+    for (int k = 0; k <= ORACLE_MAX_LEVEL; k++)
+        if (grids[k].built) free_grid(&grids[k]);
+    return 0;
+}
+
+/* Solve statistics, mirrored by a ctypes structure in oracle/__init__.py. */
+typedef struct {
+    int32_t passes;
+    int32_t pad;
+    int64_t todo_per_pass[ORACLE_MAX_PASSES];
+    int64_t unconverged;
+    int64_t exceeded;
+    int64_t pair_evals;
+} oracle_stats;
+
+/* One smoothing-length solve over one particle set for the listed targets.
+ * h_inout holds the starting h per target on entry and the last evaluated h on exit.
+ * status_out per target: 0 converged, 1 not converged, 2 h exceeds box. */
+static int solve_set(const pset *ps, int64_t n_targets, const int64_t *targets, double nngb,
+                     double tol, int max_iter, int mode, double *h_inout, double *rho_out,
+                     double *nw_out, int64_t *count_out, int32_t *status_out,
+                     oracle_stats *st)
+{
+    size_t cap = (size_t)(n_targets > 0 ? n_targets : 1);
+    double *h = (double *)malloc(cap * sizeof(double));     /* h for the next evaluation */
+    double *hlo = (double *)malloc(cap * sizeof(double));
+    double *hhi = (double *)malloc(cap * sizeof(double));
+    int64_t *todo = (int64_t *)malloc(cap * sizeof(int64_t));
+    int32_t *again = (int32_t *)malloc(cap * sizeof(int32_t));
+    if (!h || !hlo || !hhi || !todo || !again) {
+        free(h); free(hlo); free(hhi); free(todo); free(again);
+        return -1;
+    }
+    bucket_grid grids[ORACLE_MAX_LEVEL + 1];
+    memset(grids, 0, sizeof(grids));
+    double half_box = 0.5 * fmin(ps->box[0], fmin(ps->box[1], ps->box[2]));
+
+    int64_t ntodo = n_targets;
+    for (int64_t t = 0; t < n_targets; t++) {
+        h[t] = h_inout[t];
+        hlo[t] = 0.0;
+        hhi[t] = HUGE_VAL;
+        todo[t] = t;
+        again[t] = 0;
+        status_out[t] = ORC_NOT_CONVERGED;
+    }
+    int pass = 0;
+    int rc = 0;
+    while (ntodo > 0 && pass < max_iter) {
+        if (pass < ORACLE_MAX_PASSES) st->todo_per_pass[pass] = ntodo;
+        if (mode == 0) {
+            for (int64_t k = 0; k < ntodo && rc == 0; k++) {
+                int lv = level_for(ps, h[todo[k]]);
+                if (!grids[lv].built && build_grid(ps, lv, &grids[lv]) != 0) rc = -1;
+            }
+            if (rc) break;
+        }
+        int64_t pairs = 0;
+        /* The lockless scheme: dynamic scheduling over the todo list only. */
+        #pragma omp parallel for schedule(dynamic, 16) reduction(+ : pairs)
+        for (int64_t k = 0; k < ntodo; k++) {
+            int64_t t = todo[k];
+            int64_t i = targets ? targets[t] : t;
+            double hc = h[t];
+            acc_t a;
+            if (mode == 0) eval_grid(ps, &grids[level_for(ps, hc)], i, hc, 0.0, &a);
+            else eval_brute(ps, i, hc, 0.0, &a);
+            double rho, nw, dnw;
+            finish(hc, &a, &rho, &nw, &dnw);
+            pairs += a.count;
+            h_inout[t] = hc; /* outputs always describe the last evaluation */
+            rho_out[t] = rho;
+            nw_out[t] = nw;
+            count_out[t] = a.count;
+            again[t] = 0;
+            if (fabs(nw - nngb) <= tol) {
+                status_out[t] = ORC_OK;
+                continue;
+            }
+            if (nw < nngb) hlo[t] = hc;
+            else hhi[t] = hc;
+            double hn = hc;
+            int take = 0;
+            if (dnw > 0.0) {
+                hn = hc - (nw - nngb) / dnw;
+                take = hn > hlo[t] && hn < hhi[t] && hn >= 0.5 * hc && hn <= 2.0 * hc;
+            }
+            if (!take) {
+                int has_lo = hlo[t] > 0.0, has_hi = hhi[t] < HUGE_VAL;
+                if (has_lo && has_hi) hn = 0.5 * (hlo[t] + hhi[t]);
+                else if (has_lo) hn = hc * ORACLE_GROWTH;
+                else hn = hc / ORACLE_GROWTH;
+            }
+            if (ps->periodic && hn >= half_box) {
+                status_out[t] = ORC_EXCEEDS_BOX;
+                continue;
+            }
+            h[t] = hn;
+            again[t] = 1;
+        }
+        if (rc) break;
+        st->pair_evals += pairs;
+        /* mark_for_recomputation: the next todo list keeps the unconverged, in order */
+        int64_t nn = 0;
+        for (int64_t k = 0; k < ntodo; k++)
+            if (again[todo[k]]) todo[nn++] = todo[k];
+        ntodo = nn;
+        pass++;
+    }
+    st->passes = pass;
+    int64_t unconv = 0, exc = 0;
+    for (int64_t t = 0; t < n_targets; t++) {
+        if (status_out[t] == ORC_NOT_CONVERGED) unconv++;
+        if (status_out[t] == ORC_EXCEEDS_BOX) exc++;
+    }
+    st->unconverged += unconv;
+    st->exceeded += exc;
+    for (int k = 0; k <= ORACLE_MAX_LEVEL; k++)
+        if (grids[k].built) free_grid(&grids[k]);
+    free(h); free(hlo); free(hhi); free(todo); free(again);
+    return rc;
+}
+
+/* Periodic (or single non-periodic) solve for the listed targets (NULL: all). */
+int oracle_solve(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                 const double *box, int periodic, double nngb, double tol, int max_iter,
+                 int64_t n_targets, const int64_t *targets, int mode, double *h_inout,
+                 double *rho, double *nw, int64_t *count, int32_t *status, oracle_stats *st)
+{
+    pset ps;
+    setup_pset(&ps, n, x, y, z, m, box, periodic);
+    if (n_targets < 0) n_targets = n;
+    memset(st, 0, sizeof(*st));
+    return solve_set(&ps, n_targets, targets, nngb, tol, max_iter, mode, h_inout, rho, nw, count,
+                     status, st);
+}
+
+/* Batch of independent non-periodic groups; group g owns [offsets[g], offsets[g+1]).
+ * All arrays are flattened in group order; per-group nngb and tol. */
+int oracle_batch_solve(int64_t n_groups, const int64_t *offsets, const double *x, const double *y,
+                       const double *z, const double *m, const double *nngb, const double *tol,
+                       int max_iter, int mode, double *h_inout, double *rho, double *nw,
+                       int64_t *count, int32_t *status, oracle_stats *st)
+{
+    memset(st, 0, sizeof(*st));
+    const double nobox[3] = {0.0, 0.0, 0.0};
+    for (int64_t g = 0; g < n_groups; g++) {
+        int64_t s = offsets[g], e = offsets[g + 1];
+        if (e <= s) continue;
+        pset ps;
+        setup_pset(&ps, e - s, x + s, y + s, z + s, m + s, nobox, 0);
+        oracle_stats gs;
+        memset(&gs, 0, sizeof(gs));
+        int rc = solve_set(&ps, e - s, NULL, nngb[g], tol[g], max_iter, mode, h_inout + s, rho + s,
+                           nw + s, count + s, status + s, &gs);
+        if (rc) return rc;
+        if (gs.passes > st->passes) st->passes = gs.passes;
+        for (int p = 0; p < ORACLE_MAX_PASSES; p++) st->todo_per_pass[p] += gs.todo_per_pass[p];
+        st->unconverged += gs.unconverged;
+        st->exceeded += gs.exceeded;
+        st->pair_evals += gs.pair_evals;
+    }
+    return 0;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,59 @@
+"""O(N^2) brute-force neighbour sums in NumPy, used to pin the oracle's neighbour search.
+
+For every target i and every particle j it forms the minimum-image separation (periodic)
+or the plain separation, keeps the pairs with r < h_i (self included) and sums the M4
+kernel.  It shares no code with the oracle or with the CUDA path.  The kernel shape is
+written out again here, so this module pins the neighbour search, the periodic images and
+the sums, not the kernel formula (the kernel is pinned by its own property tests).
+"""
+import math
+
+import numpy as np
+
+
+def _w(q):
+    q = np.asarray(q, dtype=np.float64)
+    inner = 1.0 - 6.0 * q * q + 6.0 * q * q * q
+    a = 1.0 - q
+    outer = 2.0 * a * a * a
+    return np.where(q <= 0.5, inner, np.where(q < 1.0, outer, 0.0))
+
+
+def _mqdw(q):
+    q = np.asarray(q, dtype=np.float64)
+    inner = 12.0 * q * q - 18.0 * q * q * q
+    a = 1.0 - q
+    outer = 6.0 * q * a * a
+    return np.where(q <= 0.5, inner, np.where(q < 1.0, outer, 0.0))
+
+
+def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, chunk=256):
+    """rho, N_w, dN_w/dh, count for each target at its own h, by direct summation."""
+    pos = np.asarray(pos, dtype=np.float64)
+    mass = np.asarray(mass, dtype=np.float64)
+    n = pos.shape[1]
+    tg = np.arange(n) if targets is None else np.asarray(targets)
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), tg.shape)
+    box = np.asarray(box, dtype=np.float64)
+    rho = np.empty(tg.shape[0])
+    nw = np.empty(tg.shape[0])
+    dnw = np.empty(tg.shape[0])
+    count = np.empty(tg.shape[0], dtype=np.int64)
+    for s in range(0, tg.shape[0], chunk):
+        idx = tg[s:s + chunk]
+        hh = h[s:s + chunk][:, None]
+        d = pos[:, None, :] - pos[:, idx][:, :, None]  # (3, c, n): r_j - r_i
+        if periodic:
+            d = d - box[:, None, None] * np.round(d / box[:, None, None])
+        r2 = (d * d).sum(axis=0)
+        inside = r2 < hh * hh
+        r = np.sqrt(r2)
+        q = np.where(inside, r / hh, 1.0)
+        w = np.where(inside, _w(q), 0.0)
+        dw = np.where(inside, _mqdw(q), 0.0)
+        hv = hh[:, 0]
+        rho[s:s + chunk] = (w * mass[None, :]).sum(axis=1) * 8.0 / (math.pi * hv ** 3)
+        nw[s:s + chunk] = 32.0 / 3.0 * w.sum(axis=1)
+        dnw[s:s + chunk] = 32.0 / 3.0 * dw.sum(axis=1) / hv
+        count[s:s + chunk] = inside.sum(axis=1)
+    return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
