@@ -1,0 +1,393 @@
+"""Benchmark: converged SPH particles/s for the density / smoothing-length solve on GB300.
+
+One step = one pass of the whole hot path on one batch of input already resident in HBM:
+sph_sort (fixed-point Morton keys, radix sort, gather, cell tables) followed by
+sph_density_solve (all density passes, h updates and compactions until every particle is
+in its band, then the scatter to caller order).  The workload is the 1,048,576-particle
+Plummer-cluster set (64 spheres of scale radius 0.01 holding 70 % of the particles plus a
+uniform background, periodic unit box, Nngb = 64 +- 2), generated from a fixed seed.
+
+Printed (one JSON line, rank 0): value = converged particles/s over all ranks, the FP32 +
+compensated path; e2e = the same through the C ABI with the inputs in pinned host memory and
+the host<->device copies inside the timed region; roofline of the density kernel (FP32 ALU
+bound); the plain FP64 GPU solve beside it; the FP64 CPU oracle timed on this host on a
+bounded sample (cpu_baseline).  ``--impl reference`` times only the oracle.
+
+Multi-GPU: one process per GPU (torchrun), each solving its own replica of the workload
+(the single periodic system is not sharded: replicas only), value = all particles / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "converged SPH particles/s (rho+h)"
+UNIT = "particles/s"
+# FP32 operations the method needs per in-h pair (definition in DESIGN.md, "Roofline"):
+# 3 differences, r^2 (3 mul + 2 add), 1 compare, 1 sqrt, q (1 mul), w (7), -q w' (5),
+# m*w (1), three sums (3) = 27, +1 for the integer count.
+FLOP_PER_PAIR = 28
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", default="c2", help="c1|c2|c3|c5 (c2 is the headline workload)")
+    ap.add_argument("--n", type=int, default=0, help="override the particle count")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle targets (0 = auto)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1612_06090_gb300 import inputs
+
+    kw = {"n": args.n} if args.n else {}
+    wl = inputs.make(args.config, **kw)
+    desc = {
+        "c1": "uniform periodic box",
+        "c2": "64 Plummer spheres (a=0.01, 70%) + uniform background, periodic unit box",
+        "c3": "log-normal density field (64^3 Gaussian, P(k)~k^-2, sigma_ln=2), periodic unit box",
+        "c5": "4096 Plummer clumps (a log-uniform in [1e-3,1e-2], 70%) + background, periodic unit box",
+    }[args.config]
+    return wl, f"{args.config}: {wl.n:,} particles, {desc}, Nngb={wl.nngb:g}+-{wl.tol:g}, M4 kernel"
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region --------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- the CPU oracle on a bounded sample --------------------------------------------------------
+
+def cpu_baseline(wl, n_targets):
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.default_rng(99)
+    tg = np.sort(rng.choice(wl.n, size=min(n_targets, wl.n), replace=False))
+    t0 = time.perf_counter()
+    r = oracle.solve(wl.pos, wl.mass, wl.h0[tg], box=wl.box, periodic=wl.periodic, nngb=wl.nngb,
+                     tol=wl.tol, targets=tg)
+    dt = time.perf_counter() - t0
+    return {"value": len(tg) / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{len(tg):,} random targets of the same workload solved against all "
+                      f"{wl.n:,} particles (FP64, bucket grids, OpenMP dynamic over the todo list); "
+                      f"{dt:.1f} s wall incl. grid builds",
+            "seconds": dt, "passes": r["stats"]["passes"]}
+
+
+def run_reference(args):
+    rank, world = dist_init(args)
+    if rank != 0:
+        return
+    wl, desc = workload(args)
+    n_t = args.cpu_sample or max(1024, wl.n // 16)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, max(256, n_t // 8))
+    times = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(wl, n_t)
+        times.append(last["seconds"])
+    per_step = statistics.mean(times)
+    value = min(n_t, wl.n) / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "n": wl.n, "sample_targets": min(n_t, wl.n)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---- the CUDA path ------------------------------------------------------------------------
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from paper_1612_06090_gb300 import binding as B
+
+    rank, world = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl, desc = workload(args)
+    n = wl.n
+    stream = torch.cuda.current_stream()
+
+    pos = torch.as_tensor(wl.pos, device=dev)
+    mass = torch.as_tensor(wl.mass, device=dev)
+    h0 = torch.as_tensor(wl.h0, device=dev)
+    h = torch.empty_like(h0)
+    rho = torch.empty_like(h0)
+    nw = torch.empty_like(h0)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def make(prec):
+        s = B.Solver(n, stream=stream, precision=prec, box=wl.box, nngb=wl.nngb, tol=wl.tol)
+        s.n = n  # sorted through the raw ABI below
+        return s
+
+    def step(s, stats_out=None):
+        h.copy_(h0)
+        st = s._check(B.sph_sort(s.ctx, n, pos.data_ptr(), mass.data_ptr()))
+        stats = B.SphStats()
+        st = B.sph_density_solve(s.ctx, h.data_ptr(), rho.data_ptr(), cnt.data_ptr(), nw.data_ptr(), stats)
+        if st != B.SPH_OK:
+            raise B.SphError(st, B.sph_last_error(s.ctx))
+        if stats_out is not None:
+            stats_out.append(stats.to_dict())
+
+    def timed(s, steps, warmup):
+        for _ in range(warmup):
+            step(s)
+        torch.cuda.synchronize()
+        stats = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()  # evict L2 between steps (outside the per-step events)
+            ev[k][0].record(stream)
+            step(s, stats)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - w0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, stats, wall
+
+    # ---- FP32 + compensated: the headline ----
+    s32 = make(B.SPH_PREC_FP32_KAHAN)
+    with ClockSampler(local) as clk:
+        ms32, st32, wall32 = timed(s32, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_step = statistics.mean(ms32)
+    t_max = max_over_ranks(ms_step, world)
+    value = world * n / (t_max / 1e3)
+
+    # roofline of the density kernel from its own events (library-recorded on this stream)
+    dens_ms = sum(s["density_ms"] for s in st32)
+    dens_launch = sum(s["density_launches"] for s in st32)
+    pairs = sum(s["pair_evals"] for s in st32)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    achieved = pairs * FLOP_PER_PAIR / (dens_ms / 1e3) / 1e12 if dens_ms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_density<false> (FP32 pair loop)", "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
+            "flop_per_pair": FLOP_PER_PAIR, "pairs_per_step": pairs // max(1, len(st32)),
+            "density_ms_per_step": dens_ms / max(1, len(st32)),
+            "density_launches_per_step": dens_launch / max(1, len(st32)),
+            "density_share_of_step": dens_ms / max(1e-9, sum(ms32))}
+    launches = sum(s["kernel_launches"] for s in st32)
+
+    # ---- plain FP64 GPU solve at the same accuracy target ----
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = make(B.SPH_PREC_FP64)
+        ms64, st64, _ = timed(s64, args.fp64_steps, 1)
+        t64 = max_over_ranks(statistics.mean(ms64), world)
+        fp64 = {"value": world * n / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64,
+                "density_ms_per_step": sum(s["density_ms"] for s in st64) / len(st64)}
+        # agreement of the two GPU precisions on this workload
+        h.copy_(h0)
+        s32_ref = s64.solve(h0)
+        h64 = s32_ref["h"].cpu().numpy()
+        s64.close()
+        r32 = s32.solve(h0)
+        h32 = r32["h"].cpu().numpy()
+        rho32 = r32["rho"].cpu().numpy()
+        rho64 = s32_ref["rho"].cpu().numpy()
+        same = np.abs(h32 - h64) <= 1e-5 * h64
+        fp64["fp32_vs_fp64"] = {
+            "same_trajectory_frac": float(same.mean()),
+            "max_rel_rho_err_same_trajectory": float(np.max(np.abs(rho32[same] - rho64[same]) / rho64[same])),
+            "max_rel_h_err": float(np.max(np.abs(h32 - h64) / h64)),
+        }
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hp = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in
+              (("pos", pos), ("mass", mass), ("h0", h0))}
+        hp["pos"].copy_(torch.as_tensor(wl.pos))
+        hp["mass"].copy_(torch.as_tensor(wl.mass))
+        hp["h0"].copy_(torch.as_tensor(wl.h0))
+        outp = {"h": torch.empty(n, dtype=torch.float64).pin_memory(),
+                "rho": torch.empty(n, dtype=torch.float64).pin_memory(),
+                "count": torch.empty(n, dtype=torch.int32).pin_memory()}
+        dpos, dmass, dh = torch.empty_like(pos), torch.empty_like(mass), torch.empty_like(h0)
+
+        def e2e_step():
+            dpos.copy_(hp["pos"], non_blocking=True)
+            dmass.copy_(hp["mass"], non_blocking=True)
+            dh.copy_(hp["h0"], non_blocking=True)
+            s32._check(B.sph_sort(s32.ctx, n, dpos.data_ptr(), dmass.data_ptr()))
+            st = B.sph_density_solve(s32.ctx, dh.data_ptr(), rho.data_ptr(), cnt.data_ptr(), 0, None)
+            if st != B.SPH_OK:
+                raise B.SphError(st, B.sph_last_error(s32.ctx))
+            outp["h"].copy_(dh, non_blocking=True)
+            outp["rho"].copy_(rho, non_blocking=True)
+            outp["count"].copy_(cnt, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier(world)
+        te = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": world * n / te, "unit": UNIT, "ms_per_step": te * 1e3,
+               "h2d_bytes_per_step": n * (24 + 8 + 8), "d2h_bytes_per_step": n * (8 + 8 + 4)}
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu and world == 1:
+        cpu = cpu_baseline(wl, args.cpu_sample or max(2048, n // 8))
+        cpu.pop("seconds", None)
+        cpu.pop("passes", None)
+
+    s32.close()
+    if rank == 0:
+        st0 = st32[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "precision": "FP32 pairs + Kahan sums, FP64 h update",
+                       "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "passes": st0["passes"], "todo_per_pass": st0["todo_per_pass"],
+                       "sort_ms": st0["sort_ms"], "solve_ms": st0["solve_ms"],
+                       "wall_s_timed_region": wall32},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
+            "gpu_launches": launches, "clocks": clocks,
+            "paper_context": "paper speed-ups optimised vs original CPU code: 2.6x IVB, 13.7x KNC, 19.1x KNL",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * sph.h -- C ABI of the GB300 SPH density / smoothing-length solver.
+ *
+ * The library computes, for every particle i, the SPH density by kernel interpolation
+ * (Baruffa et al., arXiv:1612.06090, Eq. 1, read in gather form):
+ *     rho_i = sum_{j : r_ij < h_i} m_j W(r_ij, h_i),
+ * with the M4 cubic-spline kernel W(r, h) = 8/(pi h^3) w(r/h), the self pair included,
+ * together with the weighted neighbour count N_w = (4 pi / 3) h^3 sum_j W(r_ij, h), its
+ * derivative dN_w/dh and the integer count n_i = #{j : r_ij < h_i}.  It adjusts each h_i
+ * (Newton step with a bisection fallback) until |N_w - Nngb| <= tol, recomputing only
+ * the particles still off target on every pass (Sec. IV-A, Listings 2 and 3:
+ * mark_for_recomputation over a "todo" list with dynamic scheduling).  The paper states
+ * no update rule; the one implemented is:
+ *     converged iff |N_w - Nngb| <= tol; bracket: N_w < Nngb -> h_lo = h, else h_hi = h;
+ *     Newton h' = h - (N_w - Nngb)/N_w' taken iff N_w' > 0, h_lo < h' < h_hi and
+ *     h/2 <= h' <= 2h; otherwise (h_lo + h_hi)/2 when both bounds are set, h * 2^(1/3)
+ *     when only h_lo is set, h / 2^(1/3) when only h_hi is set.  The h update and the
+ *     convergence test always run in IEEE FP64.
+ *
+ * Memory and streams.  Every pointer argument named *_dev is DEVICE memory owned by the
+ * caller, valid for the duration of the call and ordered on the context's stream.  A
+ * context owns all scratch memory; it allocates it once, in sph_create, for `capacity`
+ * particles, and never allocates afterwards.  One context per stream; a context is not
+ * thread-safe.  Results are returned in the caller's particle order.
+ *
+ * Errors.  Every call returns an sph_status; nothing is thrown and nothing exits.
+ * Argument errors are detected on the host before any device work is queued.  Errors
+ * found on the device (non-finite or out-of-box positions, non-positive h) come back
+ * through a device status word as SPH_ERR_DEVICE_STATUS.  sph_last_error() gives a
+ * one-line description of the last failure on a context.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_INVALID_ARG = 1,    /* a bad argument, detected on the host                  */
+    SPH_ERR_CUDA = 2,           /* a CUDA runtime call failed (no device, launch error)   */
+    SPH_ERR_OOM = 3,            /* n or the group count exceeds the context's capacity    */
+    SPH_ERR_NOT_SORTED = 4,     /* sph_density_solve/_eval before a successful sph_sort   */
+    SPH_ERR_H_EXCEEDS_BOX = 5,  /* periodic: some h had to reach min(box)/2               */
+    SPH_ERR_NOT_CONVERGED = 6,  /* max_iter passes ran out for some particles             */
+    SPH_ERR_DEVICE_STATUS = 7,  /* the device flagged bad input (NaN/Inf/out-of-box)      */
+    SPH_ERR_UNSUPPORTED = 8     /* a valid option this build does not implement          */
+} sph_status;
+
+typedef enum { SPH_KERNEL_M4 = 0, SPH_KERNEL_WENDLAND_C6 = 1 } sph_kernel;
+
+/* FP64: every pair in FP64, exactly as the FP64 reference formulae are written.
+ * FP32_KAHAN: pair distances and kernel weights in FP32 on offsets formed from
+ * 32-bit fixed-point coordinates, sums compensated (Kahan), h update in FP64. */
+typedef enum { SPH_PREC_FP64 = 0, SPH_PREC_FP32_KAHAN = 1 } sph_precision;
+
+typedef struct {
+    double box[3];       /* periodic box lengths (> 0); ignored by sph_batch_solve        */
+    int32_t periodic;    /* 1: periodic box, minimum image (positions in [0, box));
+                            0: open boundaries                                          */
+    int32_t kernel;      /* sph_kernel; only SPH_KERNEL_M4 is implemented                 */
+    double nngb;         /* target weighted count (> 32/3, the self term)                 */
+    double tol;          /* band half-width (>= 0)                                        */
+    int32_t max_iter;    /* passes, 1..64                                                  */
+    int32_t precision;   /* sph_precision                                                  */
+    int32_t use_graph;   /* 1: run the pass loop as a CUDA graph with a device-side loop  */
+    int32_t reserved;    /* must be 0                                                      */
+    const char *tune_cache; /* autotuner cache file, or NULL for built-in defaults         */
+} sph_params;
+
+#define SPH_MAX_PASSES 64
+
+typedef struct {
+    int32_t passes;                          /* evaluation passes run                     */
+    int32_t kernel_launches;                 /* CUDA kernels of the call and of its sort  */
+    int64_t todo_per_pass[SPH_MAX_PASSES];   /* particles evaluated in each pass          */
+    int64_t unconverged;                     /* still off target after max_iter passes    */
+    int64_t exceeded;                        /* stopped because h reached min(box)/2      */
+    int64_t pair_evals;                      /* sum over passes of in-h pairs (self incl.) */
+    double sort_ms;                          /* device time of the sort stage             */
+    double solve_ms;                         /* device time of the solve                  */
+    double density_ms;                       /* device time inside the density kernels    */
+    int32_t density_launches;                /* density-kernel launches                   */
+    int32_t pad;
+} sph_stats;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
+ * on the current CUDA device, with scratch for up to `capacity` particles (and up to
+ * `capacity` batch groups).  Allocates all device memory the context will ever use.
+ * Errors: INVALID_ARG (NULL params/out, capacity < 1 or > 2^31 - 2^20, bad params),
+ * UNSUPPORTED (Wendland C6), CUDA (no device), OOM (device allocation failed). */
+sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_stream, sph_ctx **out);
+
+/* Replace the solve parameters of a context (precision, nngb, tol, max_iter, use_graph).
+ * Changing box or periodic invalidates the sorted state (sph_sort must run again). */
+sph_status sph_set_params(sph_ctx *ctx, const sph_params *params);
+
+/* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix
+ * sort, gather into a sorted SoA, cell tables).  pos_xyz_dev holds three planes of n
+ * doubles each (x[0..n), y[0..n), z[0..n)); mass_dev holds n doubles > 0.  Periodic
+ * positions must lie in [0, box[d]).  Errors: INVALID_ARG (NULL, n < 1), OOM
+ * (n > capacity), CUDA; bad positions or masses -> DEVICE_STATUS. */
+sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const double *mass_dev);
+
+/* Solve h for the particles of the last sph_sort.  h_inout_dev: n doubles, the starting
+ * h on entry (0 < h < min(box)/2 when periodic) and the final h on exit; rho_out_dev:
+ * n doubles; count_out_dev: n int32 (integer neighbour count, self included);
+ * nw_out_dev: n doubles or NULL (weighted count N_w).  An unconverged particle gets the
+ * last h it was evaluated at and the density/counts of that evaluation.  stats may be
+ * NULL.  Returns OK, NOT_CONVERGED or H_EXCEEDS_BOX (outputs are written in all three
+ * cases), or NOT_SORTED / INVALID_ARG / DEVICE_STATUS / CUDA. */
+sph_status sph_density_solve(sph_ctx *ctx, double *h_inout_dev, double *rho_out_dev,
+                             int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats);
+
+/* One density evaluation at fixed h (no iteration) for the particles of the last
+ * sph_sort.  h_dev: n doubles in caller order.  Outputs (caller order): rho, integer
+ * count, N_w and dN_w/dh; nw/dnw may be NULL. */
+sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_dev,
+                            int32_t *count_out_dev, double *nw_out_dev, double *dnw_out_dev);
+
+/* Solve many independent non-periodic groups in one pass loop.  Group g owns the
+ * particles [offsets[g], offsets[g+1]) of the flattened arrays; offsets_dev holds
+ * n_groups + 1 int64 (offsets[0] = 0, non-decreasing); nngb_dev and tol_dev hold one
+ * double per group.  pos_xyz_dev is three planes of n = offsets[n_groups] doubles.
+ * Every group is sorted, searched and iterated on its own (no box, no h limit), but all
+ * groups share each kernel launch.  Returns like sph_density_solve. */
+sph_status sph_batch_solve(sph_ctx *ctx, int64_t n_groups, const int64_t *offsets_dev,
+                           const double *pos_xyz_dev, const double *mass_dev,
+                           const double *nngb_dev, const double *tol_dev, double *h_inout_dev,
+                           double *rho_out_dev, int32_t *count_out_dev, double *nw_out_dev,
+                           sph_stats *stats);
+
+/* Release every resource of the context (NULL is ignored). */
+void sph_destroy(sph_ctx *ctx);
+
+/* Static description of a status code. */
+const char *sph_status_string(sph_status status);
+
+/* One-line description of the last error on the context ("" if none). */
+const char *sph_last_error(const sph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

@@ -1,0 +1,289 @@
+"""ctypes binding of libsph.so (include/sph.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.  The raw
+functions keep the C names and take device pointers as Python ints (``tensor.data_ptr()``)
+and a CUDA stream handle (``torch.cuda.current_stream().cuda_stream``).  ``Solver`` wraps a
+context for torch tensors.  If libsph.so is missing the binding raises; nothing falls back
+to the CPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsph.so")
+
+# sph_status
+SPH_OK = 0
+SPH_ERR_INVALID_ARG = 1
+SPH_ERR_CUDA = 2
+SPH_ERR_OOM = 3
+SPH_ERR_NOT_SORTED = 4
+SPH_ERR_H_EXCEEDS_BOX = 5
+SPH_ERR_NOT_CONVERGED = 6
+SPH_ERR_DEVICE_STATUS = 7
+SPH_ERR_UNSUPPORTED = 8
+# sph_kernel / sph_precision
+SPH_KERNEL_M4 = 0
+SPH_KERNEL_WENDLAND_C6 = 1
+SPH_PREC_FP64 = 0
+SPH_PREC_FP32_KAHAN = 1
+SPH_MAX_PASSES = 64
+
+EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sph_density_eval",
+            "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error")
+
+
+class SphParams(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("nngb", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tune_cache", ctypes.c_char_p),
+    ]
+
+
+class SphStats(ctypes.Structure):
+    _fields_ = [
+        ("passes", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int32),
+        ("todo_per_pass", ctypes.c_int64 * SPH_MAX_PASSES),
+        ("unconverged", ctypes.c_int64),
+        ("exceeded", ctypes.c_int64),
+        ("pair_evals", ctypes.c_int64),
+        ("sort_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+        ("density_ms", ctypes.c_double),
+        ("density_launches", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+    def to_dict(self) -> dict:
+        p = int(self.passes)
+        return {
+            "passes": p,
+            "kernel_launches": int(self.kernel_launches),
+            "todo_per_pass": [int(v) for v in self.todo_per_pass[: max(0, min(p, SPH_MAX_PASSES))]],
+            "unconverged": int(self.unconverged),
+            "exceeded": int(self.exceeded),
+            "pair_evals": int(self.pair_evals),
+            "sort_ms": float(self.sort_ms),
+            "solve_ms": float(self.solve_ms),
+            "density_ms": float(self.density_ms),
+            "density_launches": int(self.density_launches),
+        }
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsph.so (built by paper_1612_06090_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1612_06090_gb300.build` (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.sph_create.restype = i32
+    L.sph_create.argtypes = [ctypes.POINTER(SphParams), i64, vp, ctypes.POINTER(vp)]
+    L.sph_set_params.restype = i32
+    L.sph_set_params.argtypes = [vp, ctypes.POINTER(SphParams)]
+    L.sph_sort.restype = i32
+    L.sph_sort.argtypes = [vp, i64, vp, vp]
+    L.sph_density_solve.restype = i32
+    L.sph_density_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(SphStats)]
+    L.sph_density_eval.restype = i32
+    L.sph_density_eval.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.sph_batch_solve.restype = i32
+    L.sph_batch_solve.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SphStats)]
+    L.sph_destroy.restype = None
+    L.sph_destroy.argtypes = [vp]
+    L.sph_status_string.restype = ctypes.c_char_p
+    L.sph_status_string.argtypes = [i32]
+    L.sph_last_error.restype = ctypes.c_char_p
+    L.sph_last_error.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def make_params(box=(1.0, 1.0, 1.0), periodic=True, nngb=64.0, tol=2.0, max_iter=64,
+                precision=SPH_PREC_FP32_KAHAN, use_graph=False, kernel=SPH_KERNEL_M4,
+                tune_cache=None) -> SphParams:
+    p = SphParams()
+    for d in range(3):
+        p.box[d] = float(box[d])
+    p.periodic = int(bool(periodic))
+    p.kernel = int(kernel)
+    p.nngb = float(nngb)
+    p.tol = float(tol)
+    p.max_iter = int(max_iter)
+    p.precision = int(precision)
+    p.use_graph = int(bool(use_graph))
+    p.reserved = 0
+    p.tune_cache = tune_cache.encode() if tune_cache else None
+    return p
+
+
+# ---- raw C calls (same names as the ABI) -------------------------------------------------
+
+def sph_create(params: SphParams, capacity: int, stream: int = 0):
+    out = ctypes.c_void_p()
+    st = lib().sph_create(ctypes.byref(params), int(capacity), ctypes.c_void_p(stream or None),
+                          ctypes.byref(out))
+    return st, out.value
+
+
+def sph_set_params(ctx, params: SphParams) -> int:
+    return lib().sph_set_params(ctypes.c_void_p(ctx), ctypes.byref(params))
+
+
+def sph_sort(ctx, n: int, pos_xyz_ptr: int, mass_ptr: int) -> int:
+    return lib().sph_sort(ctypes.c_void_p(ctx), int(n), ctypes.c_void_p(pos_xyz_ptr or None),
+                          ctypes.c_void_p(mass_ptr or None))
+
+
+def sph_density_solve(ctx, h_ptr: int, rho_ptr: int, count_ptr: int, nw_ptr: int = 0, stats=None) -> int:
+    return lib().sph_density_solve(ctypes.c_void_p(ctx), ctypes.c_void_p(h_ptr or None),
+                                   ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(count_ptr or None),
+                                   ctypes.c_void_p(nw_ptr or None),
+                                   ctypes.byref(stats) if stats is not None else None)
+
+
+def sph_density_eval(ctx, h_ptr: int, rho_ptr: int, count_ptr: int, nw_ptr: int = 0, dnw_ptr: int = 0) -> int:
+    return lib().sph_density_eval(ctypes.c_void_p(ctx), ctypes.c_void_p(h_ptr or None),
+                                  ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(count_ptr or None),
+                                  ctypes.c_void_p(nw_ptr or None), ctypes.c_void_p(dnw_ptr or None))
+
+
+def sph_batch_solve(ctx, n_groups: int, offsets_ptr: int, pos_xyz_ptr: int, mass_ptr: int,
+                    nngb_ptr: int, tol_ptr: int, h_ptr: int, rho_ptr: int, count_ptr: int,
+                    nw_ptr: int = 0, stats=None) -> int:
+    v = lambda p: ctypes.c_void_p(p or None)  # noqa: E731
+    return lib().sph_batch_solve(ctypes.c_void_p(ctx), int(n_groups), v(offsets_ptr), v(pos_xyz_ptr),
+                                 v(mass_ptr), v(nngb_ptr), v(tol_ptr), v(h_ptr), v(rho_ptr),
+                                 v(count_ptr), v(nw_ptr),
+                                 ctypes.byref(stats) if stats is not None else None)
+
+
+def sph_destroy(ctx) -> None:
+    if ctx:
+        lib().sph_destroy(ctypes.c_void_p(ctx))
+
+
+def sph_status_string(status: int) -> str:
+    return lib().sph_status_string(int(status)).decode()
+
+
+def sph_last_error(ctx) -> str:
+    r = lib().sph_last_error(ctypes.c_void_p(ctx) if ctx else None)
+    return r.decode() if r else ""
+
+
+# ---- convenience wrapper for torch tensors ------------------------------------------------
+
+class SphError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{sph_status_string(status)} ({status}): {message}")
+        self.status = status
+
+
+class Solver:
+    """One context on the current CUDA device and stream, driven with torch tensors.
+
+    Positions are a (3, N) float64 CUDA tensor (x, y, z planes), masses (N,) float64.
+    solve()/batch_solve() return a dict with h, rho, count, nw, status and stats; a solve
+    that ends NOT_CONVERGED or H_EXCEEDS_BOX still returns (check ``status``); any other
+    failure raises SphError.
+    """
+
+    def __init__(self, capacity: int, stream=None, **params):
+        import torch
+
+        self._torch = torch
+        self.params = make_params(**params)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        st, ctx = sph_create(self.params, capacity, s.cuda_stream)
+        if st != SPH_OK:
+            raise SphError(st, "sph_create failed")
+        self.ctx = ctx
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, ok=(SPH_OK,)):
+        if st not in ok:
+            raise SphError(st, sph_last_error(self.ctx))
+        return st
+
+    def set_params(self, **params):
+        self.params = make_params(**params)
+        self._check(sph_set_params(self.ctx, self.params))
+
+    def sort(self, pos, mass):
+        pos = pos.contiguous()
+        mass = mass.contiguous()
+        self._pos, self._mass = pos, mass  # keep alive until the stream has used them
+        self.n = int(mass.shape[0])
+        self._check(sph_sort(self.ctx, self.n, pos.data_ptr(), mass.data_ptr()))
+
+    def solve(self, h0, out=None):
+        torch = self._torch
+        h = h0.clone() if out is None else out["h"].copy_(h0)
+        rho = torch.empty_like(h) if out is None else out["rho"]
+        count = torch.empty(self.n, dtype=torch.int32, device=h.device) if out is None else out["count"]
+        nw = torch.empty_like(h) if out is None else out["nw"]
+        stats = SphStats()
+        st = self._check(sph_density_solve(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
+                                           nw.data_ptr(), stats),
+                         ok=(SPH_OK, SPH_ERR_NOT_CONVERGED, SPH_ERR_H_EXCEEDS_BOX))
+        return {"h": h, "rho": rho, "count": count, "nw": nw, "status": st, "stats": stats.to_dict()}
+
+    def evaluate(self, h):
+        torch = self._torch
+        rho = torch.empty_like(h)
+        nw = torch.empty_like(h)
+        dnw = torch.empty_like(h)
+        count = torch.empty(self.n, dtype=torch.int32, device=h.device)
+        self._check(sph_density_eval(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
+                                     nw.data_ptr(), dnw.data_ptr()))
+        return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
+
+    def batch_solve(self, offsets, pos, mass, h0, nngb, tol):
+        torch = self._torch
+        offsets = offsets.contiguous()
+        pos = pos.contiguous()
+        mass = mass.contiguous()
+        nngb = nngb.contiguous()
+        tol = tol.contiguous()
+        n = int(mass.shape[0])
+        h = h0.clone()
+        rho = torch.empty_like(h)
+        nw = torch.empty_like(h)
+        count = torch.empty(n, dtype=torch.int32, device=h.device)
+        stats = SphStats()
+        st = self._check(sph_batch_solve(self.ctx, int(offsets.shape[0] - 1), offsets.data_ptr(),
+                                         pos.data_ptr(), mass.data_ptr(), nngb.data_ptr(), tol.data_ptr(),
+                                         h.data_ptr(), rho.data_ptr(), count.data_ptr(), nw.data_ptr(),
+                                         stats),
+                         ok=(SPH_OK, SPH_ERR_NOT_CONVERGED, SPH_ERR_H_EXCEEDS_BOX))
+        return {"h": h, "rho": rho, "count": count, "nw": nw, "status": st, "stats": stats.to_dict()}

@@ -1,0 +1,561 @@
+// sph_capi.cu -- the C ABI (include/sph.h): context, one-time scratch arena, argument
+// checks, and the host orchestration of sort -> pass loop -> scatter on the context's
+// stream.  No CUDA type crosses the ABI; every failure becomes an sph_status plus a
+// per-context message.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sph.h"
+#include "sph_kernels.cuh"
+
+using namespace sph;
+
+struct sph_ctx {
+    sph_params params{};
+    std::string tune_cache;
+    int64_t capacity = 0;
+    int64_t max_groups = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+
+    // sorted state
+    bool sorted = false;
+    int64_t n = 0;
+    KeyLayout kl{};
+    int which = 0;  // key/idx buffer holding the sorted order
+    SegInfo seg_host{};
+
+    // device arena
+    void *arena = nullptr;
+    uint64_t *key[2] = {nullptr, nullptr};
+    int32_t *idx[2] = {nullptr, nullptr};
+    int32_t *hist = nullptr, *hist_off = nullptr, *scan_aux = nullptr;
+    uint4 *pfix = nullptr;
+    double4_32a *pdbl = nullptr;
+    int32_t *ctab = nullptr;
+    SegInfo *segs = nullptr;
+    double *h = nullptr, *hlo = nullptr, *hhi = nullptr, *e_h = nullptr, *e_rho = nullptr,
+           *e_nw = nullptr, *e_dnw = nullptr;
+    int32_t *e_cnt = nullptr, *todo[2] = {nullptr, nullptr}, *flags = nullptr, *items = nullptr;
+    int32_t *tsize = nullptr, *toff = nullptr;
+    DevState *ds = nullptr;
+
+    // pinned host mirrors
+    DevState *ds_host = nullptr;
+    SegInfo *seg_pinned = nullptr;
+    int64_t *i64_pinned = nullptr;
+
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t dev_ev[2 * SPH_MAX_PASSES] = {};  // around each density launch
+    int launches = 0;
+    int sort_launches = 0;  // kernels of the last sort stage
+    int grid_cap = 0;
+    int density_grid[2] = {0, 0};
+};
+
+namespace {
+
+constexpr int64_t kMaxCapacity = (1ll << 31) - (1ll << 20);
+constexpr int64_t kMaxGroupsCap = 1ll << 20;
+
+sph_status fail(sph_ctx *c, sph_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return s;
+}
+
+sph_status cuda_fail(sph_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, SPH_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CU(ctx, expr, where)                                                                  \
+    do {                                                                                      \
+        cudaError_t e__ = (expr);                                                             \
+        if (e__ != cudaSuccess) return cuda_fail((ctx), e__, (where));                        \
+    } while (0)
+
+sph_status check_params(sph_ctx *c, const sph_params *p)
+{
+    if (!p) return fail(c, SPH_ERR_INVALID_ARG, "params is NULL");
+    if (p->kernel == SPH_KERNEL_WENDLAND_C6)
+        return fail(c, SPH_ERR_UNSUPPORTED, "the Wendland C6 kernel is not implemented");
+    if (p->kernel != SPH_KERNEL_M4) return fail(c, SPH_ERR_INVALID_ARG, "unknown kernel %d", p->kernel);
+    if (p->precision != SPH_PREC_FP64 && p->precision != SPH_PREC_FP32_KAHAN)
+        return fail(c, SPH_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+    if (p->periodic != 0 && p->periodic != 1) return fail(c, SPH_ERR_INVALID_ARG, "periodic must be 0 or 1");
+    if (p->periodic)
+        for (int d = 0; d < 3; d++)
+            if (!(p->box[d] > 0.0 && p->box[d] <= DBL_MAX))
+                return fail(c, SPH_ERR_INVALID_ARG, "box[%d] must be finite and > 0", d);
+    if (!(p->nngb > 32.0 / 3.0 && p->nngb <= 1e9))
+        return fail(c, SPH_ERR_INVALID_ARG, "nngb must exceed the self term 32/3 (got %g)", p->nngb);
+    if (!(p->tol >= 0.0 && p->tol <= DBL_MAX)) return fail(c, SPH_ERR_INVALID_ARG, "tol must be >= 0");
+    if (p->max_iter < 1 || p->max_iter > SPH_MAX_PASSES)
+        return fail(c, SPH_ERR_INVALID_ARG, "max_iter must be in [1, %d]", SPH_MAX_PASSES);
+    if (p->use_graph != 0 && p->use_graph != 1) return fail(c, SPH_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+    if (p->reserved != 0) return fail(c, SPH_ERR_INVALID_ARG, "reserved must be 0");
+    return SPH_OK;
+}
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Carve every buffer out of one allocation; with base == nullptr only the size is computed.
+size_t carve(sph_ctx *c, char *base)
+{
+    const int64_t cap = c->capacity;
+    const int64_t hs = radix_hist_size(cap);
+    const int64_t aux = scan_aux_size(std::max<int64_t>(cap, hs)) + 8;
+    const int64_t ctab_cap = 3 * cap + 2;
+    const int64_t gcap = c->max_groups;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return p;
+    };
+    for (int k = 0; k < 2; k++) c->key[k] = (uint64_t *)take(cap * 8);
+    for (int k = 0; k < 2; k++) c->idx[k] = (int32_t *)take(cap * 4);
+    c->hist = (int32_t *)take(hs * 4);
+    c->hist_off = (int32_t *)take(hs * 4);
+    c->scan_aux = (int32_t *)take(aux * 4);
+    c->pfix = (uint4 *)take(cap * 16);
+    c->pdbl = (double4_32a *)take(cap * 32);
+    c->ctab = (int32_t *)take(ctab_cap * 4);
+    c->segs = (SegInfo *)take((gcap + 1) * sizeof(SegInfo));
+    c->h = (double *)take(cap * 8);
+    c->hlo = (double *)take(cap * 8);
+    c->hhi = (double *)take(cap * 8);
+    c->e_h = (double *)take(cap * 8);
+    c->e_rho = (double *)take(cap * 8);
+    c->e_nw = (double *)take(cap * 8);
+    c->e_dnw = (double *)take(cap * 8);
+    c->e_cnt = (int32_t *)take(cap * 4);
+    for (int k = 0; k < 2; k++) c->todo[k] = (int32_t *)take(cap * 4);
+    c->flags = (int32_t *)take(cap * 4);
+    c->items = (int32_t *)take((cap + 1) * 4);
+    c->tsize = (int32_t *)take((gcap + 1) * 4);
+    c->toff = (int32_t *)take((gcap + 1) * 4);
+    c->ds = (DevState *)take(sizeof(DevState));
+    return off;
+}
+
+SortArgs sort_args(sph_ctx *c)
+{
+    SortArgs a{};
+    for (int k = 0; k < 2; k++) {
+        a.key[k] = c->key[k];
+        a.idx[k] = c->idx[k];
+    }
+    a.hist = c->hist;
+    a.hist_off = c->hist_off;
+    a.scan_aux = c->scan_aux;
+    a.pfix = c->pfix;
+    a.pdbl = c->pdbl;
+    a.ctab = c->ctab;
+    a.segs = c->segs;
+    a.ds = c->ds;
+    a.kl = c->kl;
+    a.grid_cap = c->grid_cap;
+    a.launches = &c->launches;
+    return a;
+}
+
+SolveArgs solve_args(sph_ctx *c)
+{
+    SolveArgs a{};
+    a.pfix = c->pfix;
+    a.pdbl = c->pdbl;
+    a.key = c->key[c->which];
+    a.idx = c->idx[c->which];
+    a.segs = c->segs;
+    a.ctab = c->ctab;
+    a.kl = c->kl;
+    a.n = c->n;
+    a.h = c->h;
+    a.hlo = c->hlo;
+    a.hhi = c->hhi;
+    a.e_h = c->e_h;
+    a.e_rho = c->e_rho;
+    a.e_nw = c->e_nw;
+    a.e_dnw = c->e_dnw;
+    a.e_cnt = c->e_cnt;
+    a.todo[0] = c->todo[0];
+    a.todo[1] = c->todo[1];
+    a.flags = c->flags;
+    a.items = c->items;
+    a.scan_aux = c->scan_aux;
+    a.ds = c->ds;
+    a.grid_cap = c->grid_cap;
+    a.precision = c->params.precision;
+    a.density_grid = c->density_grid[c->params.precision == SPH_PREC_FP64 ? 0 : 1];
+    a.gmax = 32;
+    a.launches = &c->launches;
+    return a;
+}
+
+// Level of the dense cell table: the finest level with at most one cell per particle.
+int table_level(int64_t n, int lmax)
+{
+    int lc = 0;
+    while (lc < lmax && lc < 10 && (1ll << (3 * (lc + 1))) <= n) lc++;
+    return lc;
+}
+
+sph_status read_state(sph_ctx *c)
+{
+    CU(c, cudaMemcpyAsync(c->ds_host, c->ds, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream),
+       "reading the device state");
+    CU(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    return SPH_OK;
+}
+
+sph_status device_status_error(sph_ctx *c, int bits)
+{
+    std::string what;
+    if (bits & kBadPosition) what += " non-finite or out-of-box position;";
+    if (bits & kBadMass) what += " non-positive or non-finite mass;";
+    if (bits & kBadH) what += " h not in (0, min(box)/2) or bad group nngb/tol;";
+    if (bits & 8) what += " internal cell-count guard;";
+    return fail(c, SPH_ERR_DEVICE_STATUS, "device flagged the input:%s", what.c_str());
+}
+
+// The pass loop shared by sph_density_solve and sph_batch_solve.
+sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *count_out,
+                     double *nw_out, sph_stats *stats)
+{
+    cudaStream_t st = c->stream;
+    const int launches0 = c->launches;
+    SolveArgs a = solve_args(c);
+    CU(c, cudaEventRecord(c->ev[2], st), "event");
+    CU(c, cudaMemsetAsync(c->ds, 0, sizeof(DevState), st), "clearing the device state");
+    CU(c, launch_solve_init(a, h_inout, c->params.max_iter, st), "solve init");
+    sph_status s = read_state(c);
+    if (s != SPH_OK) return s;
+    if (c->ds_host->status) return device_status_error(c, c->ds_host->status);
+
+    int cur = 0;
+    int passes_run = 0;
+    for (int pass = 0; pass < c->params.max_iter; pass++) {
+        a.dens_ev[0] = c->dev_ev[2 * pass];
+        a.dens_ev[1] = c->dev_ev[2 * pass + 1];
+        CU(c, launch_pass(a, cur, true, st), "density pass");
+        passes_run = pass + 1;
+        CU(c, cudaMemcpyAsync(&c->ds_host->todo_count, &c->ds->todo_count, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st),
+           "reading the todo count");
+        CU(c, cudaStreamSynchronize(st), "synchronising the pass");
+        cur = 1 - cur;
+        if (c->ds_host->todo_count == 0) break;
+    }
+    CU(c, launch_scatter(a, h_inout, rho_out, count_out, nw_out, nullptr, st), "scatter");
+    CU(c, cudaEventRecord(c->ev[3], st), "event");
+    s = read_state(c);
+    if (s != SPH_OK) return s;
+    const DevState &d = *c->ds_host;
+    if (d.status) return device_status_error(c, d.status);
+    if (stats) {
+        stats->passes = d.pass;
+        stats->kernel_launches = c->launches - launches0 + c->sort_launches;
+        for (int k = 0; k < SPH_MAX_PASSES; k++) stats->todo_per_pass[k] = k < d.pass ? d.todo_per_pass[k] : 0;
+        stats->unconverged = d.todo_count;
+        stats->exceeded = d.exceeded;
+        stats->pair_evals = (int64_t)d.pair_evals;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+        stats->solve_ms = ms;
+        double dms = 0.0;
+        for (int k = 0; k < passes_run; k++) {
+            float m = 0.f;
+            if (cudaEventElapsedTime(&m, c->dev_ev[2 * k], c->dev_ev[2 * k + 1]) == cudaSuccess) dms += m;
+        }
+        stats->density_ms = dms;
+        stats->density_launches = passes_run;
+    }
+    if (d.exceeded > 0)
+        return fail(c, SPH_ERR_H_EXCEEDS_BOX, "%d particles needed h >= min(box)/2", d.exceeded);
+    if (d.todo_count > 0)
+        return fail(c, SPH_ERR_NOT_CONVERGED, "%d particles unconverged after %d passes", d.todo_count,
+                    d.pass);
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sph_status_string(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_INVALID_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA error";
+    case SPH_ERR_OOM: return "capacity exceeded or device allocation failed";
+    case SPH_ERR_NOT_SORTED: return "sph_sort must run first";
+    case SPH_ERR_H_EXCEEDS_BOX: return "h reached half the periodic box";
+    case SPH_ERR_NOT_CONVERGED: return "not converged within max_iter passes";
+    case SPH_ERR_DEVICE_STATUS: return "the device flagged invalid input";
+    case SPH_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char *sph_last_error(const sph_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_stream, sph_ctx **out)
+{
+    if (!out) return SPH_ERR_INVALID_ARG;
+    *out = nullptr;
+    sph_status s = check_params(nullptr, params);
+    if (s != SPH_OK) return s;
+    if (capacity < 1 || capacity > kMaxCapacity) return SPH_ERR_INVALID_ARG;
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return SPH_ERR_OOM;
+    c->params = *params;
+    if (params->tune_cache) c->tune_cache = params->tune_cache;
+    c->params.tune_cache = nullptr;
+    c->capacity = capacity;
+    c->max_groups = std::min<int64_t>(capacity, kMaxGroupsCap);
+    c->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](sph_status st) {
+        sph_destroy(c);
+        return st;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(SPH_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return bail(SPH_ERR_CUDA);
+    const size_t bytes = carve(c, nullptr);
+    if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->arena = nullptr;
+        return bail(SPH_ERR_OOM);
+    }
+    carve(c, (char *)c->arena);
+    if (cudaMallocHost((void **)&c->ds_host, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->seg_pinned, sizeof(SegInfo)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->i64_pinned, 2 * sizeof(int64_t)) != cudaSuccess)
+        return bail(SPH_ERR_OOM);
+    for (int k = 0; k < 4; k++)
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(SPH_ERR_CUDA);
+    for (int k = 0; k < 2 * SPH_MAX_PASSES; k++)
+        if (cudaEventCreate(&c->dev_ev[k]) != cudaSuccess) return bail(SPH_ERR_CUDA);
+    c->grid_cap = c->num_sms * 16;
+    c->density_grid[0] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP64);
+    c->density_grid[1] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN);
+    if (cudaMemset(c->ds, 0, sizeof(DevState)) != cudaSuccess) return bail(SPH_ERR_CUDA);
+    *out = c;
+    return SPH_OK;
+}
+
+sph_status sph_set_params(sph_ctx *ctx, const sph_params *params)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    sph_status s = check_params(ctx, params);
+    if (s != SPH_OK) return s;
+    const bool geometry_changed = params->periodic != ctx->params.periodic ||
+                                  params->box[0] != ctx->params.box[0] ||
+                                  params->box[1] != ctx->params.box[1] ||
+                                  params->box[2] != ctx->params.box[2];
+    ctx->params = *params;
+    ctx->tune_cache = params->tune_cache ? params->tune_cache : "";
+    ctx->params.tune_cache = nullptr;
+    if (geometry_changed) ctx->sorted = false;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream || ctx->arena) cudaStreamSynchronize(ctx->stream);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->ds_host) cudaFreeHost(ctx->ds_host);
+    if (ctx->seg_pinned) cudaFreeHost(ctx->seg_pinned);
+    if (ctx->i64_pinned) cudaFreeHost(ctx->i64_pinned);
+    for (int k = 0; k < 4; k++)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    for (int k = 0; k < 2 * SPH_MAX_PASSES; k++)
+        if (ctx->dev_ev[k]) cudaEventDestroy(ctx->dev_ev[k]);
+    delete ctx;
+}
+
+sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const double *mass_dev)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    ctx->sorted = false;
+    if (!pos_xyz_dev || !mass_dev) return fail(ctx, SPH_ERR_INVALID_ARG, "NULL position or mass pointer");
+    if (n < 1) return fail(ctx, SPH_ERR_INVALID_ARG, "n must be >= 1 (got %lld)", (long long)n);
+    if (n > ctx->capacity)
+        return fail(ctx, SPH_ERR_OOM, "n = %lld exceeds the context capacity %lld", (long long)n,
+                    (long long)ctx->capacity);
+    if (!ctx->params.periodic)
+        return fail(ctx, SPH_ERR_UNSUPPORTED, "sph_sort needs periodic = 1; open particle sets go "
+                                              "through sph_batch_solve (one group per set)");
+    cudaStream_t st = ctx->stream;
+    const sph_params &p = ctx->params;
+    ctx->n = n;
+    ctx->kl.lmax = 21;
+    ctx->kl.seg_bits = 0;
+    ctx->kl.key_bits = 63;
+    ctx->kl.coord_bits = 32;
+    SegInfo &sg = ctx->seg_host;
+    memset(&sg, 0, sizeof(sg));
+    for (int d = 0; d < 3; d++) {
+        sg.q[d] = std::ldexp(p.box[d], -32);      // exact: a power-of-two scaling
+        sg.inv_q[d] = std::ldexp(1.0 / p.box[d], 32);
+        sg.origin[d] = 0.0;
+        sg.box[d] = p.box[d];
+    }
+    sg.nngb = p.nngb;
+    sg.tol = p.tol;
+    sg.half_box = 0.5 * std::min(p.box[0], std::min(p.box[1], p.box[2]));
+    sg.periodic = 1;
+    sg.level_c = table_level(n, ctx->kl.lmax);
+    sg.tab_off = 0;
+    sg.start = 0;
+    sg.end = (int32_t)n;
+    *ctx->seg_pinned = sg;
+    CU(ctx, cudaEventRecord(ctx->ev[0], st), "event");
+    CU(ctx, cudaMemcpyAsync(ctx->segs, ctx->seg_pinned, sizeof(SegInfo), cudaMemcpyHostToDevice, st),
+       "uploading the segment");
+    CU(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), st), "clearing the device state");
+    const int launches0 = ctx->launches;
+    SortArgs a = sort_args(ctx);
+    CU(ctx, launch_keys_periodic(a, n, pos_xyz_dev, mass_dev, sg, p.box, st), "morton keys");
+    int which = 0;
+    CU(ctx, launch_radix_sort(a, n, &which, st), "radix sort");
+    ctx->which = which;
+    CU(ctx, launch_gather_periodic(a, n, pos_xyz_dev, mass_dev, ctx->idx[which], sg, st), "gather");
+    CU(ctx, launch_cell_table(a, n, ctx->key[which], st), "cell table");
+    CU(ctx, cudaEventRecord(ctx->ev[1], st), "event");
+    ctx->sort_launches = ctx->launches - launches0;
+    sph_status s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    ctx->sorted = true;
+    return SPH_OK;
+}
+
+sph_status sph_density_solve(sph_ctx *ctx, double *h_inout_dev, double *rho_out_dev,
+                             int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!h_inout_dev || !rho_out_dev || !count_out_dev)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "NULL h, rho or count pointer");
+    if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    // the band and pass limit may have changed since the sort
+    SegInfo sg = ctx->seg_host;
+    sg.nngb = ctx->params.nngb;
+    sg.tol = ctx->params.tol;
+    *ctx->seg_pinned = sg;
+    CU(ctx, cudaMemcpyAsync(ctx->segs, ctx->seg_pinned, sizeof(SegInfo), cudaMemcpyHostToDevice,
+                            ctx->stream),
+       "uploading the segment");
+    sph_status s = run_solve(ctx, h_inout_dev, rho_out_dev, count_out_dev, nw_out_dev, stats);
+    if (stats) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) stats->sort_ms = ms;
+    }
+    return s;
+}
+
+sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_dev,
+                            int32_t *count_out_dev, double *nw_out_dev, double *dnw_out_dev)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!h_dev || !rho_out_dev || !count_out_dev)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "NULL h, rho or count pointer");
+    if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
+    cudaStream_t st = ctx->stream;
+    SolveArgs a = solve_args(ctx);
+    CU(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), st), "clearing the device state");
+    CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
+    sph_status s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    CU(ctx, launch_pass(a, 0, false, st), "density pass");
+    CU(ctx, launch_scatter(a, nullptr, rho_out_dev, count_out_dev, nw_out_dev, dnw_out_dev, st), "scatter");
+    s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    return SPH_OK;
+}
+
+sph_status sph_batch_solve(sph_ctx *ctx, int64_t n_groups, const int64_t *offsets_dev,
+                           const double *pos_xyz_dev, const double *mass_dev, const double *nngb_dev,
+                           const double *tol_dev, double *h_inout_dev, double *rho_out_dev,
+                           int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    ctx->sorted = false;
+    if (!offsets_dev || !pos_xyz_dev || !mass_dev || !nngb_dev || !tol_dev || !h_inout_dev ||
+        !rho_out_dev || !count_out_dev)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "NULL pointer argument");
+    if (n_groups < 1) return fail(ctx, SPH_ERR_INVALID_ARG, "n_groups must be >= 1");
+    if (n_groups > ctx->max_groups)
+        return fail(ctx, SPH_ERR_OOM, "n_groups = %lld exceeds the context limit %lld",
+                    (long long)n_groups, (long long)ctx->max_groups);
+    if (stats) memset(stats, 0, sizeof(*stats));
+    cudaStream_t st = ctx->stream;
+    CU(ctx, cudaMemcpyAsync(ctx->i64_pinned, offsets_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+       "reading offsets[0]");
+    CU(ctx, cudaMemcpyAsync(ctx->i64_pinned + 1, offsets_dev + n_groups, sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, st),
+       "reading offsets[n_groups]");
+    CU(ctx, cudaStreamSynchronize(st), "synchronising");
+    const int64_t n = ctx->i64_pinned[1];
+    if (ctx->i64_pinned[0] != 0) return fail(ctx, SPH_ERR_INVALID_ARG, "offsets[0] must be 0");
+    if (n < 1) return fail(ctx, SPH_ERR_INVALID_ARG, "offsets[n_groups] must be >= 1");
+    if (n > ctx->capacity)
+        return fail(ctx, SPH_ERR_OOM, "n = %lld exceeds the context capacity %lld", (long long)n,
+                    (long long)ctx->capacity);
+    ctx->n = n;
+    int seg_bits = 0;
+    while ((1ll << seg_bits) < n_groups) seg_bits++;
+    ctx->kl.seg_bits = seg_bits;
+    ctx->kl.lmax = std::min(21, (63 - seg_bits) / 3);
+    ctx->kl.key_bits = seg_bits + 3 * ctx->kl.lmax;
+    ctx->kl.coord_bits = 31;
+
+    CU(ctx, cudaEventRecord(ctx->ev[0], st), "event");
+    CU(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), st), "clearing the device state");
+    const int launches0 = ctx->launches;
+    SortArgs a = sort_args(ctx);
+    CU(ctx, launch_group_setup(a, n_groups, offsets_dev, pos_xyz_dev, n, nngb_dev, tol_dev, ctx->tsize,
+                               ctx->toff, st),
+       "group setup");
+    CU(ctx, launch_keys_open(a, n, pos_xyz_dev, mass_dev, offsets_dev, n_groups, st), "morton keys");
+    int which = 0;
+    CU(ctx, launch_radix_sort(a, n, &which, st), "radix sort");
+    ctx->which = which;
+    CU(ctx, launch_gather_open(a, n, pos_xyz_dev, mass_dev, ctx->idx[which], ctx->key[which], st), "gather");
+    CU(ctx, launch_cell_table(a, n, ctx->key[which], st), "cell table");
+    CU(ctx, cudaEventRecord(ctx->ev[1], st), "event");
+    ctx->sort_launches = ctx->launches - launches0;
+    sph_status s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    s = run_solve(ctx, h_inout_dev, rho_out_dev, count_out_dev, nw_out_dev, stats);
+    if (stats) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) stats->sort_ms = ms;
+    }
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// sph_kernels.cuh -- argument blocks and launchers of the sort and solve kernels.
+#pragma once
+
+#include "sph_common.cuh"
+
+namespace sph {
+
+// Buffers the sort stage reads and writes.
+struct SortArgs {
+    uint64_t *key[2];      // ping-pong key buffers
+    int32_t *idx[2];       // ping-pong original-index buffers
+    int32_t *hist;         // radix histograms
+    int32_t *hist_off;     // their exclusive scan
+    int32_t *scan_aux;     // scan scratch
+    uint4 *pfix;           // sorted fixed-point positions + FP32 mass
+    double4_32a *pdbl;         // sorted FP64 positions + mass
+    int32_t *ctab;         // dense cell tables of all segments
+    SegInfo *segs;         // segment descriptors (device)
+    DevState *ds;
+    KeyLayout kl;
+    int grid_cap;          // upper bound on blocks per launch
+    int *launches;         // host-side launch counter
+};
+
+int64_t radix_hist_size(int64_t n_max);
+cudaError_t launch_keys_periodic(const SortArgs &a, int64_t n, const double *pos, const double *mass,
+                                 const SegInfo &seg, const double box[3], cudaStream_t st);
+cudaError_t launch_group_setup(const SortArgs &a, int64_t n_groups, const int64_t *offsets,
+                               const double *pos, int64_t n, const double *nngb, const double *tol,
+                               int32_t *tsize, int32_t *toff, cudaStream_t st);
+cudaError_t launch_keys_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
+                             const int64_t *offsets, int64_t n_groups, cudaStream_t st);
+cudaError_t launch_radix_sort(const SortArgs &a, int64_t n, int *which, cudaStream_t st);
+cudaError_t launch_gather_periodic(const SortArgs &a, int64_t n, const double *pos,
+                                   const double *mass, const int32_t *idx, const SegInfo &seg,
+                                   cudaStream_t st);
+cudaError_t launch_gather_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
+                               const int32_t *idx, const uint64_t *key, cudaStream_t st);
+cudaError_t launch_cell_table(const SortArgs &a, int64_t n, const uint64_t *key, cudaStream_t st);
+
+// Buffers and state of the solve.
+struct SolveArgs {
+    // sorted particle data
+    const uint4 *pfix;
+    const double4_32a *pdbl;
+    const uint64_t *key;
+    const int32_t *idx;        // sorted position -> caller index
+    const SegInfo *segs;
+    const int32_t *ctab;
+    KeyLayout kl;
+    int64_t n;
+    // iteration state (sorted order)
+    double *h;                 // h of the next evaluation
+    double *hlo, *hhi;         // brackets
+    double *e_h;               // h of the last evaluation
+    double *e_rho, *e_nw, *e_dnw;
+    int32_t *e_cnt;
+    int32_t *todo[2];          // ping-pong todo lists (sorted positions)
+    int32_t *flags;            // per-todo-entry scratch flags
+    int32_t *items;            // work-item starts (indices into the todo list)
+    int32_t *scan_aux;
+    DevState *ds;
+    int grid_cap;
+    int density_grid;          // persistent blocks of the density kernels
+    int gmax;                  // targets per work item (<= 32)
+    int precision;             // sph_precision
+    int *launches;
+    cudaEvent_t dens_ev[2];    // optional events recorded around the density launch
+};
+
+cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_iter, cudaStream_t st);
+// One evaluation pass over todo[cur]; when `update`, also the h update and the next todo
+// list (todo[1 - cur]).
+cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t st);
+cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, int32_t *count_out,
+                           double *nw_out, double *dnw_out, cudaStream_t st);
+
+// sph_density.cu
+cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st);
+int density_blocks_per_sm(int precision);
+
+}  // namespace sph

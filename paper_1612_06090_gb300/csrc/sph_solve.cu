@@ -1,0 +1,224 @@
+// sph_solve.cu -- the pass loop around the density kernel: work items, the h update with
+// its convergence test, the todo-list compaction and the scatter back to caller order.
+//
+// This is the lockless scheme of Sec. IV-A (Listing 3) on the GPU: every pass runs only
+// over the todo list of unconverged particles; mark_for_recomputation becomes the h-update
+// kernel plus a stable compaction that writes the next todo list; the error check that the
+// listing hoists out of the loop is a device status word read once the pass loop is done.
+#include <cfloat>
+#include <cmath>
+
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr double kGrowth = 1.2599210498948732;  // 2^(1/3), the bisection-free growth step
+
+__device__ __forceinline__ int seg_of(uint64_t k, const KeyLayout &kl)
+{
+    return kl.seg_bits > 0 ? (int)(k >> (3 * kl.lmax)) : 0;
+}
+
+// Grouping level of a target: the finest octree level whose cell edge is at least h.
+// `big` marks targets whose cell plus h reaches half the periodic range; those form
+// single-target work items so every staged offset is a minimum-image offset.
+__device__ __forceinline__ void bucket_of(uint64_t k, double h, const SegInfo &S,
+                                          const KeyLayout &kl, int &lvl, uint64_t &prefix,
+                                          bool &big)
+{
+    const int cb = kl.coord_bits;
+    const double maxinv = fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
+    const double hu = ceil(h * maxinv);
+    int l = kl.lmax;
+    while (l > 0 && (double)(1ll << (cb - l)) < hu) l--;
+    lvl = l;
+    prefix = k >> (3 * (kl.lmax - l));
+    big = S.periodic && ((double)(1ll << (cb - l)) + hu >= (double)(1ll << (cb - 1)));
+}
+
+__global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int max_iter)
+{
+    const int64_t n = a.n;
+    int bad = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a.idx[p];
+        const double hv = h_in[i];
+        const SegInfo &S = a.segs[seg_of(a.key[p], a.kl)];
+        if (!(hv > 0.0 && hv <= DBL_MAX) || (S.periodic && hv >= S.half_box)) bad |= kBadH;
+        a.h[p] = hv;
+        a.hlo[p] = 0.0;
+        a.hhi[p] = HUGE_VAL;
+        a.e_h[p] = hv;
+        a.todo[0][p] = (int32_t)p;
+    }
+    if (bad) atomicOr(&a.ds->status, bad);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ds->todo_count = (int32_t)n;
+        a.ds->todo_next = 0;
+        a.ds->n_items = 0;
+        a.ds->item_head = 0;
+        a.ds->exceeded = 0;
+        a.ds->pass = 0;
+        a.ds->max_iter = max_iter;
+        a.ds->loop_flag = n > 0 ? 1 : 0;
+        a.ds->pair_evals = 0ull;
+        for (int k = 0; k < kMaxPasses; k++) a.ds->todo_per_pass[k] = 0;
+    }
+}
+
+__global__ void k_pass_begin(DevState *ds)
+{
+    ds->item_head = 0;
+    ds->todo_next = 0;
+    if (ds->pass < kMaxPasses) ds->todo_per_pass[ds->pass] = ds->todo_count;
+}
+
+__global__ void k_pass_end(DevState *ds)
+{
+    ds->todo_count = ds->todo_next;
+    ds->pass += 1;
+    ds->loop_flag = (ds->todo_count > 0 && ds->pass < ds->max_iter) ? 1 : 0;
+}
+
+// Work-item heads: a new item starts at every multiple of gmax, whenever the grouping
+// bucket (level + octree cell at that level, segment included) changes, and around
+// single-target ("big") entries.
+__global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
+{
+    const int T = a.ds->todo_count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int p = todo[t];
+        const uint64_t k = a.key[p];
+        int l;
+        uint64_t pre;
+        bool big;
+        bucket_of(k, a.h[p], a.segs[seg_of(k, a.kl)], a.kl, l, pre, big);
+        int head = (t % a.gmax == 0) || big;
+        if (!head) {
+            const int pp = todo[t - 1];
+            const uint64_t kp = a.key[pp];
+            int lp;
+            uint64_t prep;
+            bool bigp;
+            bucket_of(kp, a.h[pp], a.segs[seg_of(kp, a.kl)], a.kl, lp, prep, bigp);
+            head = bigp || lp != l || prep != pre;
+        }
+        a.flags[t] = head;
+    }
+}
+
+// mark_for_recomputation: band test, bracket, Newton or fallback, box limit (FP64, IEEE
+// roundings spelled out so no product is fused into an FMA).
+__global__ void k_h_update(SolveArgs a, const int32_t *__restrict__ todo)
+{
+    const int T = a.ds->todo_count;
+    int exceeded = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int p = todo[t];
+        const SegInfo &S = a.segs[seg_of(a.key[p], a.kl)];
+        const double h = a.e_h[p];
+        const double nw = a.e_nw[p];
+        const double dnw = a.e_dnw[p];
+        int alive = 0;
+        if (!(fabs(__dsub_rn(nw, S.nngb)) <= S.tol)) {
+            double lo = a.hlo[p], hi = a.hhi[p];
+            if (nw < S.nngb) lo = h;
+            else hi = h;
+            double hn = h;
+            bool take = false;
+            if (dnw > 0.0) {
+                hn = __dsub_rn(h, __ddiv_rn(__dsub_rn(nw, S.nngb), dnw));
+                take = hn > lo && hn < hi && hn >= __dmul_rn(0.5, h) && hn <= __dmul_rn(2.0, h);
+            }
+            if (!take) {
+                const bool has_lo = lo > 0.0, has_hi = hi < HUGE_VAL;
+                if (has_lo && has_hi) hn = __dmul_rn(0.5, __dadd_rn(lo, hi));
+                else if (has_lo) hn = __dmul_rn(h, kGrowth);
+                else hn = __ddiv_rn(h, kGrowth);
+            }
+            a.hlo[p] = lo;
+            a.hhi[p] = hi;
+            if (S.periodic && hn >= S.half_box) {
+                exceeded++;
+            } else {
+                a.h[p] = hn;
+                alive = 1;
+            }
+        }
+        a.flags[t] = alive;
+    }
+    exceeded = warp_sum(exceeded);
+    if ((threadIdx.x & 31) == 0 && exceeded) atomicAdd(&a.ds->exceeded, exceeded);
+}
+
+__global__ void k_scatter(SolveArgs a, double *__restrict__ h_out, double *__restrict__ rho_out,
+                          int32_t *__restrict__ count_out, double *__restrict__ nw_out,
+                          double *__restrict__ dnw_out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a.idx[p];
+        if (h_out) h_out[i] = a.e_h[p];
+        rho_out[i] = a.e_rho[p];
+        count_out[i] = a.e_cnt[p];
+        if (nw_out) nw_out[i] = a.e_nw[p];
+        if (dnw_out) dnw_out[i] = a.e_dnw[p];
+    }
+}
+
+int blocks_for(int64_t n, int cap)
+{
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_iter, cudaStream_t st)
+{
+    k_solve_init<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a, h_in, max_iter);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t st)
+{
+    const int32_t *todo = a.todo[cur];
+    const int grid = blocks_for(a.n, a.grid_cap);
+    k_pass_begin<<<1, 1, 0, st>>>(a.ds);
+    k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
+    if (a.launches) *a.launches += 2;
+    // item starts = positions of the head flags
+    cudaError_t e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->todo_count,
+                                &a.ds->n_items, a.scan_aux, a.grid_cap, st, a.launches);
+    if (e != cudaSuccess) return e;
+    if (a.dens_ev[0]) cudaEventRecord(a.dens_ev[0], st);
+    e = launch_density(a, todo, st);
+    if (e != cudaSuccess) return e;
+    if (a.dens_ev[1]) cudaEventRecord(a.dens_ev[1], st);
+    if (!update) return cudaGetLastError();
+    k_h_update<<<grid, kThreads, 0, st>>>(a, todo);
+    if (a.launches) *a.launches += 1;
+    e = compact_i32(a.flags, todo, a.todo[1 - cur], nullptr, a.n, &a.ds->todo_count, &a.ds->todo_next,
+                    a.scan_aux, a.grid_cap, st, a.launches);
+    if (e != cudaSuccess) return e;
+    k_pass_end<<<1, 1, 0, st>>>(a.ds);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, int32_t *count_out,
+                           double *nw_out, double *dnw_out, cudaStream_t st)
+{
+    k_scatter<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a, h_out, rho_out, count_out, nw_out,
+                                                                 dnw_out);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace sph

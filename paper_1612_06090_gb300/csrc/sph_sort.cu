@@ -1,0 +1,410 @@
+// sph_sort.cu -- spatial ordering: fixed-point coordinates, Morton keys, LSD radix sort,
+// gather into the sorted SoA and the dense per-segment cell tables.
+//
+// The paper's neighbour search walks a Barnes-Hut octree stored as a flat array (Sec. II-A);
+// here the octree is implicit: particles sorted by Morton key make every octree cell a
+// contiguous range, found in O(1) from a dense start table at one level per segment and by
+// binary search on the keys below it.  The gather into a compact sorted SoA plays the role
+// of the paper's AoS->SoA gather (Sec. IV-B).
+#include <cfloat>
+#include <cmath>
+
+#include "sph_common.cuh"
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSubTile = 2048;        // keys per warp in the radix passes
+constexpr int kSortThreads = 256;     // 8 warps per block
+
+// Periodic fixed point: nearest multiple of q = L / 2^32, wrapped (L itself maps to 0).
+__device__ __forceinline__ uint32_t fix_periodic(double x, double inv_q)
+{
+    double t = rint(x * inv_q);
+    if (!(t >= 0.0)) t = 0.0;  // also catches NaN (flagged separately)
+    if (t >= 4294967296.0) t -= 4294967296.0;
+    if (t >= 4294967296.0) t = 0.0;
+    return (uint32_t)(unsigned long long)t;
+}
+
+// Open boundaries: nearest multiple of q above the origin, clamped to [0, 2^31).
+__device__ __forceinline__ uint32_t fix_open(double x, double origin, double inv_q)
+{
+    double t = rint((x - origin) * inv_q);
+    if (!(t >= 0.0)) t = 0.0;
+    if (t > 2147483647.0) t = 2147483647.0;
+    return (uint32_t)t;
+}
+
+__global__ void k_keys_periodic(int64_t n, const double *__restrict__ pos,
+                                const double *__restrict__ mass, SegInfo seg, KeyLayout kl,
+                                double box_x, double box_y, double box_z,
+                                uint64_t *__restrict__ key, int32_t *__restrict__ idx,
+                                DevState *ds)
+{
+    const int shift = kl.coord_bits - kl.lmax;
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x = pos[i], y = pos[n + i], z = pos[2 * n + i], m = mass[i];
+        if (!(x >= 0.0 && x < box_x && y >= 0.0 && y < box_y && z >= 0.0 && z < box_z))
+            bad |= kBadPosition;
+        if (!(m > 0.0 && m <= DBL_MAX)) bad |= kBadMass;
+        uint32_t X = fix_periodic(x, seg.inv_q[0]);
+        uint32_t Y = fix_periodic(y, seg.inv_q[1]);
+        uint32_t Z = fix_periodic(z, seg.inv_q[2]);
+        key[i] = morton3(X >> shift, Y >> shift, Z >> shift);
+        idx[i] = (int32_t)i;
+    }
+    if (bad) atomicOr(&ds->status, bad);
+}
+
+// Group of particle i from the offsets (binary search: last g with offsets[g] <= i).
+__device__ __forceinline__ int group_of(const int64_t *__restrict__ offsets, int64_t n_groups,
+                                        int64_t i)
+{
+    int64_t lo = 0, hi = n_groups - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return (int)lo;
+}
+
+__global__ void k_keys_open(int64_t n, const double *__restrict__ pos,
+                            const double *__restrict__ mass, const int64_t *__restrict__ offsets,
+                            int64_t n_groups, const SegInfo *__restrict__ segs, KeyLayout kl,
+                            uint64_t *__restrict__ key, int32_t *__restrict__ idx, DevState *ds)
+{
+    const int shift = kl.coord_bits - kl.lmax;
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = group_of(offsets, n_groups, i);
+        const SegInfo &s = segs[g];
+        double x = pos[i], y = pos[n + i], z = pos[2 * n + i], m = mass[i];
+        if (!(fabs(x) <= DBL_MAX && fabs(y) <= DBL_MAX && fabs(z) <= DBL_MAX)) bad |= kBadPosition;
+        if (!(m > 0.0 && m <= DBL_MAX)) bad |= kBadMass;
+        uint32_t X = fix_open(x, s.origin[0], s.inv_q[0]);
+        uint32_t Y = fix_open(y, s.origin[1], s.inv_q[1]);
+        uint32_t Z = fix_open(z, s.origin[2], s.inv_q[2]);
+        uint64_t k = morton3(X >> shift, Y >> shift, Z >> shift);
+        if (kl.seg_bits > 0) k |= (uint64_t)g << (3 * kl.lmax);
+        key[i] = k;
+        idx[i] = (int32_t)i;
+    }
+    if (bad) atomicOr(&ds->status, bad);
+}
+
+// ---------------------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits.  Each warp owns a sub-tile of kSubTile keys; the digit
+// histogram is laid out digit-major over sub-tiles so that one exclusive scan gives every
+// (digit, sub-tile) its output offset; the scatter ranks equal digits within a round of 32
+// keys with __match_any_sync, which keeps the sort stable.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t *__restrict__ key,
+                                                             int64_t n, int shift,
+                                                             int32_t *__restrict__ hist,
+                                                             int64_t n_sub)
+{
+    __shared__ int counts[kSortThreads / 32][kRadixBins];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *c = counts[warp];
+    const int64_t warps_total = (int64_t)gridDim.x * (kSortThreads / 32);
+    for (int64_t s = blockIdx.x * (int64_t)(kSortThreads / 32) + warp; s < n_sub; s += warps_total) {
+        for (int d = lane; d < kRadixBins; d += 32) c[d] = 0;
+        __syncwarp();
+        const int64_t base = s * kSubTile;
+        const int64_t end = base + kSubTile < n ? base + kSubTile : n;
+        for (int64_t i = base + lane; i < end; i += 32) {
+            int d = (int)((key[i] >> shift) & (kRadixBins - 1));
+            atomicAdd(&c[d], 1);
+        }
+        __syncwarp();
+        for (int d = lane; d < kRadixBins; d += 32) hist[(int64_t)d * n_sub + s] = c[d];
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint64_t *__restrict__ key_in, const int32_t *__restrict__ idx_in,
+    uint64_t *__restrict__ key_out, int32_t *__restrict__ idx_out, int64_t n, int shift,
+    const int32_t *__restrict__ offs, int64_t n_sub)
+{
+    __shared__ int cursor[kSortThreads / 32][kRadixBins];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *c = cursor[warp];
+    const int64_t warps_total = (int64_t)gridDim.x * (kSortThreads / 32);
+    for (int64_t s = blockIdx.x * (int64_t)(kSortThreads / 32) + warp; s < n_sub; s += warps_total) {
+        for (int d = lane; d < kRadixBins; d += 32) c[d] = offs[(int64_t)d * n_sub + s];
+        __syncwarp();
+        const int64_t base = s * kSubTile;
+        const int64_t end = base + kSubTile < n ? base + kSubTile : n;
+        for (int64_t r = base; r < end; r += 32) {
+            const int64_t i = r + lane;
+            const bool valid = i < end;
+            uint64_t k = valid ? key_in[i] : 0;
+            int32_t v = valid ? idx_in[i] : 0;
+            int d = valid ? (int)((k >> shift) & (kRadixBins - 1)) : kRadixBins + lane;
+            unsigned peers = __match_any_sync(kFull, d);
+            int rank = __popc(peers & lanemask_lt());
+            if (valid) {
+                int p = c[d] + rank;
+                key_out[p] = k;
+                idx_out[p] = v;
+            }
+            __syncwarp();
+            if (valid && rank == 0) c[d] += __popc(peers);
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void k_gather_periodic(int64_t n, const double *__restrict__ pos,
+                                  const double *__restrict__ mass,
+                                  const int32_t *__restrict__ idx, SegInfo seg,
+                                  uint4 *__restrict__ pfix, double4_32a *__restrict__ pdbl)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[p];
+        double x = pos[i], y = pos[n + i], z = pos[2 * n + i], m = mass[i];
+        uint4 f;
+        f.x = fix_periodic(x, seg.inv_q[0]);
+        f.y = fix_periodic(y, seg.inv_q[1]);
+        f.z = fix_periodic(z, seg.inv_q[2]);
+        f.w = __float_as_uint((float)m);
+        pfix[p] = f;
+        pdbl[p] = make_double4_32a(x, y, z, m);
+    }
+}
+
+__global__ void k_gather_open(int64_t n, const double *__restrict__ pos,
+                              const double *__restrict__ mass, const int32_t *__restrict__ idx,
+                              const uint64_t *__restrict__ key, const SegInfo *__restrict__ segs,
+                              KeyLayout kl, uint4 *__restrict__ pfix, double4_32a *__restrict__ pdbl)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[p];
+        const int g = kl.seg_bits > 0 ? (int)(key[p] >> (3 * kl.lmax)) : 0;
+        const SegInfo &s = segs[g];
+        double x = pos[i], y = pos[n + i], z = pos[2 * n + i], m = mass[i];
+        uint4 f;
+        f.x = fix_open(x, s.origin[0], s.inv_q[0]);
+        f.y = fix_open(y, s.origin[1], s.inv_q[1]);
+        f.z = fix_open(z, s.origin[2], s.inv_q[2]);
+        f.w = __float_as_uint((float)m);
+        pfix[p] = f;
+        pdbl[p] = make_double4_32a(x, y, z, m);
+    }
+}
+
+// Dense start table of each segment at its level_c: tab[c] = first sorted index whose
+// level-c cell is >= c, for c = 0 .. 8^level_c (the last entry is the segment end).
+__global__ void k_cell_table(int64_t n, const uint64_t *__restrict__ key,
+                             const SegInfo *__restrict__ segs, KeyLayout kl,
+                             int32_t *__restrict__ tab)
+{
+    const uint64_t mmask = kl.lmax >= 21 ? 0x7fffffffffffffffull : ((1ull << (3 * kl.lmax)) - 1);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key[p];
+        const int g = kl.seg_bits > 0 ? (int)(k >> (3 * kl.lmax)) : 0;
+        const SegInfo &s = segs[g];
+        const int sh = 3 * (kl.lmax - s.level_c);
+        const int64_t pre = (int64_t)((k & mmask) >> sh);
+        const int64_t prev = p == s.start ? -1 : (int64_t)((key[p - 1] & mmask) >> sh);
+        int32_t *t = tab + s.tab_off;
+        for (int64_t c = prev + 1; c <= pre; c++) t[c] = (int32_t)p;
+        if (p == s.end - 1) {
+            const int64_t ncell = 1ll << (3 * s.level_c);
+            for (int64_t c = pre + 1; c <= ncell; c++) t[c] = s.end;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Batch groups: bounding boxes, fixed-point frames and table sizes.
+// ---------------------------------------------------------------------------------------
+__global__ void k_group_setup(int64_t n_groups, const int64_t *__restrict__ offsets,
+                              const double *__restrict__ pos, int64_t n,
+                              const double *__restrict__ nngb, const double *__restrict__ tol,
+                              KeyLayout kl, SegInfo *__restrict__ segs,
+                              int32_t *__restrict__ tsize, DevState *ds)
+{
+    __shared__ double red[6][kSortThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const int64_t s = offsets[g], e = offsets[g + 1];
+        double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+        for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                double v = pos[d * n + i];
+                lo[d] = fmin(lo[d], v);
+                hi[d] = fmax(hi[d], v);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[d] = fmin(lo[d], __shfl_xor_sync(kFull, lo[d], o));
+                hi[d] = fmax(hi[d], __shfl_xor_sync(kFull, hi[d], o));
+            }
+            if (lane == 0) {
+                red[d][warp] = lo[d];
+                red[3 + d][warp] = hi[d];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            SegInfo si;
+            si.box[0] = si.box[1] = si.box[2] = 0.0;
+            double ext = 0.0;
+            for (int d = 0; d < 3; d++) {
+                double a = DBL_MAX, b = -DBL_MAX;
+                for (int w = 0; w < kSortThreads / 32; w++) {
+                    a = fmin(a, red[d][w]);
+                    b = fmax(b, red[3 + d][w]);
+                }
+                si.origin[d] = e > s ? a : 0.0;
+                if (e > s && b - a > ext) ext = b - a;
+            }
+            if (!(ext > 0.0)) ext = 1.0;
+            // a little slack keeps the largest coordinate strictly below 2^31 units
+            ext *= 1.0 + 1.0 / 1048576.0;
+            const double q = ext / 2147483648.0;
+            for (int d = 0; d < 3; d++) {
+                si.q[d] = q;
+                si.inv_q[d] = 1.0 / q;
+            }
+            si.nngb = nngb[g];
+            si.tol = tol[g];
+            si.half_box = HUGE_VAL;
+            si.periodic = 0;
+            const int64_t cnt = e - s;
+            int lc = 0;
+            while (lc < kl.lmax - 1 && (1ll << (3 * (lc + 1))) <= cnt) lc++;
+            si.level_c = lc;
+            si.tab_off = 0;
+            si.start = (int32_t)s;
+            si.end = (int32_t)e;
+            si.pad = 0;
+            segs[g] = si;
+            tsize[g] = (int32_t)((1ll << (3 * lc)) + 1);
+            if (!(si.nngb > 32.0 / 3.0) || !(si.tol >= 0.0) || e < s) atomicOr(&ds->status, kBadH);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_group_tab_off(int64_t n_groups, const int32_t *__restrict__ toff,
+                                SegInfo *__restrict__ segs)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups;
+         g += (int64_t)gridDim.x * blockDim.x)
+        segs[g].tab_off = toff[g];
+}
+
+int blocks_for(int64_t n, int threads, int cap)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+int64_t radix_hist_size(int64_t n_max) { return (int64_t)kRadixBins * ((n_max + kSubTile - 1) / kSubTile + 1); }
+
+cudaError_t launch_keys_periodic(const SortArgs &a, int64_t n, const double *pos, const double *mass,
+                                 const SegInfo &seg, const double box[3], cudaStream_t st)
+{
+    k_keys_periodic<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(
+        n, pos, mass, seg, a.kl, box[0], box[1], box[2], a.key[0], a.idx[0], a.ds);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_setup(const SortArgs &a, int64_t n_groups, const int64_t *offsets,
+                               const double *pos, int64_t n, const double *nngb, const double *tol,
+                               int32_t *tsize, int32_t *toff, cudaStream_t st)
+{
+    k_group_setup<<<blocks_for(n_groups, 1, a.grid_cap), kSortThreads, 0, st>>>(
+        n_groups, offsets, pos, n, nngb, tol, a.kl, a.segs, tsize, a.ds);
+    if (a.launches) *a.launches += 1;
+    cudaError_t e = scan_exclusive(tsize, toff, n_groups, nullptr, nullptr, a.scan_aux, a.grid_cap, st,
+                                   a.launches);
+    if (e != cudaSuccess) return e;
+    k_group_tab_off<<<blocks_for(n_groups, 256, a.grid_cap), 256, 0, st>>>(n_groups, toff, a.segs);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
+                             const int64_t *offsets, int64_t n_groups, cudaStream_t st)
+{
+    k_keys_open<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, pos, mass, offsets, n_groups,
+                                                                  a.segs, a.kl, a.key[0], a.idx[0],
+                                                                  a.ds);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+// Sorts (key[0], idx[0]) in place (ping-pong through key[1]/idx[1]); returns the buffer
+// index holding the result in *which.
+cudaError_t launch_radix_sort(const SortArgs &a, int64_t n, int *which, cudaStream_t st)
+{
+    const int64_t n_sub = (n + kSubTile - 1) / kSubTile;
+    const int warps_per_block = kSortThreads / 32;
+    int grid = blocks_for(n_sub, warps_per_block, a.grid_cap);
+    int cur = 0;
+    for (int shift = 0; shift < a.kl.key_bits; shift += kRadixBits) {
+        k_radix_hist<<<grid, kSortThreads, 0, st>>>(a.key[cur], n, shift, a.hist, n_sub);
+        if (a.launches) *a.launches += 1;
+        cudaError_t e = scan_exclusive(a.hist, a.hist_off, (int64_t)kRadixBins * n_sub, nullptr, nullptr,
+                                       a.scan_aux, a.grid_cap, st, a.launches);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<grid, kSortThreads, 0, st>>>(a.key[cur], a.idx[cur], a.key[1 - cur],
+                                                        a.idx[1 - cur], n, shift, a.hist_off, n_sub);
+        if (a.launches) *a.launches += 1;
+        cur = 1 - cur;
+    }
+    *which = cur;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_periodic(const SortArgs &a, int64_t n, const double *pos,
+                                   const double *mass, const int32_t *idx, const SegInfo &seg,
+                                   cudaStream_t st)
+{
+    k_gather_periodic<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, pos, mass, idx, seg, a.pfix,
+                                                                       a.pdbl);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
+                               const int32_t *idx, const uint64_t *key, cudaStream_t st)
+{
+    k_gather_open<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, pos, mass, idx, key, a.segs, a.kl,
+                                                                   a.pfix, a.pdbl);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_table(const SortArgs &a, int64_t n, const uint64_t *key, cudaStream_t st)
+{
+    k_cell_table<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, key, a.segs, a.kl, a.ctab);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances.  FP64 mode recomputes every pair exactly as the oracle writes it (same
+neighbour decisions, same per-pair terms), so counts are exact and rho, N_w, h agree to
+summation-order rounding (<= 1e-12 relative).  FP32 mode forms offsets from 32-bit fixed
+point coordinates (quantum box/2^32) and sums FP32 terms with compensation; rho, N_w and h
+must agree to 1e-5 relative, and integer counts may differ only by pairs the oracle finds
+within 2e-6 h of the boundary.  Band-edge particles go through the check in parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_06090_gb300 import inputs
+from tests import brute
+from tests.parity import check_eval, check_solve, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1612_06090_gb300 import binding as B  # noqa: E402
+
+FP64, FP32 = B.SPH_PREC_FP64, B.SPH_PREC_FP32_KAHAN
+DEV = torch.device("cuda:0")
+
+
+def T(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_eval(pos, mass, h, precision, box=(1.0, 1.0, 1.0)):
+    s = B.Solver(max(len(mass), 1), precision=precision, box=box)
+    s.sort(T(pos), T(mass))
+    r = s.evaluate(T(h))
+    torch.cuda.synchronize()
+    out = {k: np_(v) for k, v in r.items()}
+    s.close()
+    return out
+
+
+def gpu_solve(pos, mass, h0, precision, box=(1.0, 1.0, 1.0), nngb=64.0, tol=2.0, max_iter=64):
+    s = B.Solver(len(mass), precision=precision, box=box, nngb=nngb, tol=tol, max_iter=max_iter)
+    s.sort(T(pos), T(mass))
+    r = s.solve(T(h0))
+    torch.cuda.synchronize()
+    out = {k: (np_(v) if torch.is_tensor(v) else v) for k, v in r.items()}
+    s.close()
+    return out
+
+
+# ---- fixed-h evaluation ------------------------------------------------------------------
+
+@pytest.mark.parametrize("scale", [1.0, 0.55, 1.9])
+def test_eval_fp64_exact_against_oracle(scale):
+    wl = inputs.make("c1")
+    rng = np.random.default_rng(7)
+    h = wl.h0 * scale * rng.uniform(0.9, 1.1, size=wl.n)
+    g = gpu_eval(wl.pos, wl.mass, h, FP64)
+    o = oracle.evaluate(wl.pos, wl.mass, h)
+    check_eval(g, o, rtol=1e-12, count_exact=True)
+    assert np.max(rel_err(g["dnw"], o["dnw"])) <= 1e-11
+
+
+@pytest.mark.parametrize("scale", [1.0, 0.55, 1.9])
+def test_eval_fp32_against_oracle(scale):
+    wl = inputs.make("c1")
+    rng = np.random.default_rng(8)
+    h = wl.h0 * scale * rng.uniform(0.9, 1.1, size=wl.n)
+    g = gpu_eval(wl.pos, wl.mass, h, FP32)
+    o = oracle.evaluate(wl.pos, wl.mass, h, near_rel=2e-6)
+    check_eval(g, o, rtol=1e-5, count_exact=False, near=o["near"])
+    assert np.max(np.abs(g["dnw"] - o["dnw"]) / (np.abs(o["dnw"]) + 1.0 / h)) <= 1e-4
+
+
+def test_eval_matches_numpy_brute_force_on_adversarial_positions():
+    rng = np.random.default_rng(5)
+    k = rng.integers(0, 64, size=(3, 3000))
+    pos = k / 64.0
+    pos[:, :6] = np.array([[0, 0, 0], [1 - 2**-30, 0, 0], [0, 1 - 2**-30, 0],
+                           [0, 0, 1 - 2**-30], [0.5, 0.5, 0.5], [1 - 2**-40, 1 - 2**-40, 0.0]]).T
+    mass = rng.uniform(0.5, 1.5, size=3000)
+    h = np.full(3000, 0.1)
+    h[::3] = 1.0 / 16.0 + 1e-9
+    h[1::3] = 3.0 / 64.0 + 1e-9
+    b = brute.evaluate(pos, mass, h)
+    g = gpu_eval(pos, mass, h, FP64)
+    np.testing.assert_array_equal(g["count"], b["count"])
+    np.testing.assert_allclose(g["rho"], b["rho"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 257, 2049, 5003])
+def test_ragged_sizes(n):
+    rng = np.random.default_rng(100 + n)
+    pos = rng.uniform(0, 1, size=(3, n))
+    mass = np.full(n, 1.0 / n)
+    h = np.clip(inputs.mean_density_h(64.0, n) * rng.uniform(0.7, 1.3, n), 1e-3, 0.45)
+    g = gpu_eval(pos, mass, h, FP64)
+    o = oracle.evaluate(pos, mass, h)
+    check_eval(g, o, rtol=1e-12, count_exact=True)
+
+
+def test_anisotropic_periodic_box():
+    rng = np.random.default_rng(12)
+    box = (1.0, 2.0, 0.5)
+    n = 4000
+    pos = np.stack([rng.uniform(0, box[d], n) for d in range(3)])
+    mass = rng.uniform(0.5, 2.0, n)
+    h = np.full(n, inputs.mean_density_h(64.0, n / (box[0] * box[1] * box[2])))
+    g = gpu_eval(pos, mass, h, FP64, box=box)
+    o = oracle.evaluate(pos, mass, h, box=box)
+    check_eval(g, o, rtol=1e-12, count_exact=True)
+    g32 = gpu_eval(pos, mass, h, FP32, box=box)
+    o32 = oracle.evaluate(pos, mass, h, box=box, near_rel=2e-6)
+    check_eval(g32, o32, rtol=1e-5, count_exact=False, near=o32["near"])
+
+
+def test_lattice_density_on_gpu():
+    import json, os
+
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "lattice16.json")))
+    g1 = (np.arange(16) + 0.5) / 16.0
+    X, Y, Z = np.meshgrid(g1, g1, g1, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+    mass = np.full(4096, 1.0 / 4096)
+    h = np.full(4096, gold["h0"])
+    for prec, rt in ((FP64, 1e-13), (FP32, 2e-6)):
+        g = gpu_eval(pos, mass, h, prec)
+        assert np.all(g["count"] == gold["count_at_h0"])
+        np.testing.assert_allclose(g["rho"], gold["rho_at_h0"], rtol=rt)
+        np.testing.assert_allclose(g["nw"], gold["nw_at_h0"], rtol=rt)
+    r = gpu_solve(pos, mass, h, FP64)
+    assert r["status"] == B.SPH_OK and r["stats"]["passes"] == 1
+    assert np.all(r["h"] == gold["h0"])
+
+
+# ---- the full solve ----------------------------------------------------------------------
+
+def test_solve_fp64_config1():
+    wl = inputs.make("c1")
+    g = gpu_solve(wl.pos, wl.mass, wl.h0, FP64)
+    assert g["status"] == B.SPH_OK
+    o = oracle.solve(wl.pos, wl.mass, wl.h0)
+    check_solve(wl.pos, wl.mass, wl.box, True, 64.0, 2.0, g, o, np.arange(wl.n), rtol=1e-12,
+                delta=1e-9 * 64, max_mismatch_frac=1e-3, count_exact=True)
+    assert g["stats"]["passes"] == o["stats"]["passes"]
+    assert g["stats"]["todo_per_pass"] == o["stats"]["todo_per_pass"]
+    assert g["stats"]["pair_evals"] == o["stats"]["pair_evals"]
+
+
+def test_solve_fp32_config1():
+    wl = inputs.make("c1")
+    g = gpu_solve(wl.pos, wl.mass, wl.h0, FP32)
+    assert g["status"] == B.SPH_OK
+    o = oracle.solve(wl.pos, wl.mass, wl.h0)
+    check_solve(wl.pos, wl.mass, wl.box, True, 64.0, 2.0, g, o, np.arange(wl.n), rtol=1e-5,
+                delta=1e-5 * 64, max_mismatch_frac=0.01, count_exact=False)
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_solve_config2_sampled(precision):
+    """1,048,576 Plummer-cluster particles: the GPU solves all; the oracle solves a random
+    sample of targets against the full particle set (the solve is in gather form)."""
+    wl = inputs.make("c2")
+    g = gpu_solve(wl.pos, wl.mass, wl.h0, precision)
+    assert g["status"] == B.SPH_OK
+    rng = np.random.default_rng(2024)
+    tg = np.sort(rng.choice(wl.n, size=1500, replace=False))
+    o = oracle.solve(wl.pos, wl.mass, wl.h0[tg], targets=tg)
+    gs = {k: g[k][tg] for k in ("h", "rho", "count", "nw")}
+    rtol = 1e-12 if precision == FP64 else 1e-5
+    check_solve(wl.pos, wl.mass, wl.box, True, 64.0, 2.0, gs, o, tg, rtol=rtol,
+                delta=(1e-9 if precision == FP64 else 1e-5) * 64,
+                max_mismatch_frac=0.02, count_exact=(precision == FP64))
+
+
+def test_fp32_and_fp64_gpu_agree_config2():
+    wl = inputs.make("c2", n=1 << 18)
+    a = gpu_solve(wl.pos, wl.mass, wl.h0, FP32)
+    b = gpu_solve(wl.pos, wl.mass, wl.h0, FP64)
+    same = (rel_err(a["h"], b["h"]) <= 1e-5)
+    assert same.mean() > 0.98
+    assert np.max(rel_err(a["rho"][same], b["rho"][same])) <= 1e-5
+
+
+def test_permutation_invariance_gpu():
+    wl = inputs.make("c1")
+    perm = np.random.default_rng(3).permutation(wl.n)
+    a = gpu_solve(wl.pos, wl.mass, wl.h0, FP64)
+    b = gpu_solve(wl.pos[:, perm], wl.mass[perm], wl.h0[perm], FP64)
+    np.testing.assert_allclose(b["h"], a["h"][perm], rtol=1e-13)
+    np.testing.assert_allclose(b["rho"], a["rho"][perm], rtol=1e-13)
+    np.testing.assert_array_equal(b["count"], a["count"][perm])
+
+
+# ---- statuses and edge cases ----------------------------------------------------------------
+
+def test_single_particle_exceeds_box():
+    r = gpu_solve(np.array([[0.2], [0.2], [0.2]]), np.array([1.0]), np.array([0.01]), FP64)
+    o = oracle.solve(np.array([[0.2], [0.2], [0.2]]), np.array([1.0]), np.array([0.01]))
+    assert r["status"] == B.SPH_ERR_H_EXCEEDS_BOX
+    assert r["stats"]["exceeded"] == 1
+    assert r["h"][0] == o["h"][0]
+    assert r["rho"][0] == pytest.approx(8.0 / (math.pi * o["h"][0] ** 3), rel=1e-14)
+
+
+def test_coincident_cluster_not_converged():
+    pos = np.full((3, 100), 0.5)
+    r = gpu_solve(pos, np.full(100, 0.01), np.full(100, 0.1), FP32, max_iter=10)
+    assert r["status"] == B.SPH_ERR_NOT_CONVERGED
+    assert r["stats"]["unconverged"] == 100
+    assert r["stats"]["todo_per_pass"] == [100] * 10
+    h = 0.1
+    for _ in range(9):
+        h = h / 1.2599210498948732
+    assert np.all(r["h"] == h)
+
+
+def test_device_flags_bad_input():
+    s = B.Solver(100, precision=FP32)
+    pos = np.random.default_rng(0).uniform(0, 1, (3, 100))
+    pos[1, 7] = np.nan
+    with pytest.raises(B.SphError) as e:
+        s.sort(T(pos), T(np.ones(100)))
+    assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    pos[1, 7] = 1.0  # outside [0, 1)
+    with pytest.raises(B.SphError) as e:
+        s.sort(T(pos), T(np.ones(100)))
+    assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    pos[1, 7] = 0.5
+    s.sort(T(pos), T(np.ones(100)))
+    with pytest.raises(B.SphError) as e:
+        s.solve(T(np.full(100, 0.5)))  # h must stay below min(box)/2
+    assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    with pytest.raises(B.SphError) as e:
+        s.solve(T(np.full(100, -1.0)))
+    assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    s.close()
+
+
+def test_host_statuses_with_a_device():
+    s = B.Solver(50, precision=FP32)
+    h = T(np.full(50, 0.1))
+    rho = torch.empty(50, dtype=torch.float64, device=DEV)
+    cnt = torch.empty(50, dtype=torch.int32, device=DEV)
+    assert B.sph_density_solve(s.ctx, h.data_ptr(), rho.data_ptr(), cnt.data_ptr()) == B.SPH_ERR_NOT_SORTED
+    pos = T(np.random.default_rng(1).uniform(0, 1, (3, 60)))
+    assert B.sph_sort(s.ctx, 60, pos.data_ptr(), T(np.ones(60)).data_ptr()) == B.SPH_ERR_OOM
+    assert B.sph_sort(s.ctx, 0, pos.data_ptr(), T(np.ones(60)).data_ptr()) == B.SPH_ERR_INVALID_ARG
+    s.close()
+
+
+# ---- batched groups ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_batch_matches_oracle(precision):
+    wl = inputs.plummer_groups(n_groups=60, nmin=32, nmax=20000, seed=31)
+    s = B.Solver(wl.n, precision=precision)
+    r = s.batch_solve(T(wl.offsets, torch.int64), T(wl.pos), T(wl.mass), T(wl.h0), T(wl.nngb), T(wl.tol))
+    torch.cuda.synchronize()
+    g = {k: (np_(v) if torch.is_tensor(v) else v) for k, v in r.items()}
+    s.close()
+    assert g["status"] == B.SPH_OK
+    o = oracle.batch_solve(wl.offsets, wl.pos, wl.mass, wl.h0, wl.nngb, wl.tol)
+    assert np.all(o["status"] == 0)
+    rtol = 1e-12 if precision == FP64 else 1e-5
+    eh = rel_err(g["h"], o["h"])
+    er = rel_err(g["rho"], o["rho"])
+    mism = (eh > rtol) | (er > rtol)
+    assert mism.mean() <= 0.02
+    if precision == FP64:
+        np.testing.assert_array_equal(g["count"][~mism], o["count"][~mism])
+    # every group's answers lie in its band
+    assert np.all(np.abs(g["nw"] - 32.0) <= 1.0 + 1e-4)
+    # band-edge particles: the oracle at the GPU's h, group by group
+    for gi in range(wl.n_groups):
+        s0, e0 = wl.offsets[gi], wl.offsets[gi + 1]
+        m = np.flatnonzero(mism[s0:e0])
+        if m.size:
+            e = oracle.evaluate(wl.pos[:, s0:e0], wl.mass[s0:e0], g["h"][s0 + m], periodic=False,
+                                box=(0, 0, 0), targets=m)
+            assert np.all(np.abs(e["nw"] - 32.0) <= 1.0 + 1e-4)
+            assert np.max(rel_err(g["rho"][s0 + m], e["rho"])) <= rtol
