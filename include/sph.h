@@ -135,6 +135,33 @@ sph_status sph_batch_solve(sph_ctx *ctx, int64_t n_groups, const int64_t *offset
                            double *rho_out_dev, int32_t *count_out_dev, double *nw_out_dev,
                            sph_stats *stats);
 
+/* ---- Evaluation without any device allocation -------------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that must not call
+ * cudaMalloc/cudaFree themselves or through this library: a plugin inside a host program
+ * that owns all device memory through its own pool, or a latency-critical loop where
+ * cudaFree would stall every stream on the device.
+ *
+ * It performs sph_sort followed by sph_density_eval (fixed h, one density pass) for up to
+ * SPH_STATIC_MAX_PARTICLES periodic particles, with every intermediate buffer placed in one
+ * fixed array of device memory compiled into the library (about 5 MB, reserved on every GPU
+ * that loads the library until the process exits).  No context is involved; params gives
+ * box, periodic (must be 1), kernel (M4), precision; nngb/tol/max_iter/use_graph are unused.
+ * pos_xyz_dev (three planes of n doubles), mass_dev and h_dev are inputs in caller order;
+ * rho/count (required) and nw/dnw (nullable) are outputs in caller order; all are device
+ * memory owned by the caller.  Work runs on cuda_stream and the call returns after the
+ * stream has finished it.
+ * The first call on each device looks up the array's device address; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls whose GPU work
+ * overlaps (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: INVALID_ARG (NULL pointers, n < 1, bad box or precision), OOM (n greater than
+ * SPH_STATIC_MAX_PARTICLES; nothing is allocated instead), UNSUPPORTED (open boundaries or
+ * another kernel), CUDA, DEVICE_STATUS (bad positions, masses or h). */
+#define SPH_STATIC_MAX_PARTICLES 32768
+sph_status sph_density_eval_static(const sph_params *params, int64_t n, const double *pos_xyz_dev,
+                                   const double *mass_dev, const double *h_dev, void *cuda_stream,
+                                   double *rho_out_dev, int32_t *count_out_dev,
+                                   double *nw_out_dev, double *dnw_out_dev);
+
 /* Release every resource of the context (NULL is ignored). */
 void sph_destroy(sph_ctx *ctx);
 

@@ -32,7 +32,9 @@ SPH_PREC_FP32_KAHAN = 1
 SPH_MAX_PASSES = 64
 
 EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sph_density_eval",
-            "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error")
+            "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error",
+            "sph_density_eval_static")
+SPH_STATIC_MAX_PARTICLES = 32768
 
 
 class SphParams(ctypes.Structure):
@@ -112,6 +114,8 @@ def lib() -> ctypes.CDLL:
     L.sph_status_string.argtypes = [i32]
     L.sph_last_error.restype = ctypes.c_char_p
     L.sph_last_error.argtypes = [vp]
+    L.sph_density_eval_static.restype = i32
+    L.sph_density_eval_static.argtypes = [ctypes.POINTER(SphParams), i64, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -187,6 +191,17 @@ def sph_status_string(status: int) -> str:
 def sph_last_error(ctx) -> str:
     r = lib().sph_last_error(ctypes.c_void_p(ctx) if ctx else None)
     return r.decode() if r else ""
+
+
+def sph_density_eval_static(params: SphParams, n: int, pos_xyz_ptr: int, mass_ptr: int, h_ptr: int,
+                            stream: int, rho_ptr: int, count_ptr: int, nw_ptr: int = 0,
+                            dnw_ptr: int = 0) -> int:
+    """Sort + fixed-h evaluation with no device allocation (scratch is a fixed array in the
+    library image, up to SPH_STATIC_MAX_PARTICLES particles; calls must not overlap)."""
+    v = lambda p: ctypes.c_void_p(p or None)  # noqa: E731
+    return lib().sph_density_eval_static(ctypes.byref(params), int(n), v(pos_xyz_ptr), v(mass_ptr),
+                                         v(h_ptr), v(stream), v(rho_ptr), v(count_ptr), v(nw_ptr),
+                                         v(dnw_ptr))
 
 
 # ---- convenience wrapper for torch tensors ------------------------------------------------
