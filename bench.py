@@ -369,6 +369,8 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "passes": st0["passes"], "todo_per_pass": st0["todo_per_pass"],
                        "sort_ms": st0["sort_ms"], "solve_ms": st0["solve_ms"],
+                       "pairs_per_pass": st0["pairs_per_pass"], "pair_tests": st0["pair_tests"],
+                       "density_ms_per_pass": [round(v, 3) for v in st0["density_ms_per_pass"]],
                        "wall_s_timed_region": wall32},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
             "gpu_launches": launches, "clocks": clocks,

@@ -85,9 +85,27 @@ typedef struct {
     double density_ms;                       /* device time inside the density kernels    */
     int32_t density_launches;                /* density-kernel launches                   */
     int32_t pad;
+    int64_t pair_tests;                      /* candidate-target distance tests performed */
+    int64_t pairs_per_pass[SPH_MAX_PASSES];  /* in-h pairs of each pass                   */
+    double density_ms_per_pass[SPH_MAX_PASSES]; /* density-kernel time of each pass       */
 } sph_stats;
 
 typedef struct sph_ctx sph_ctx;
+
+/* Knobs of the spatial decomposition, set by the autotuner or by hand.  They change speed,
+ * never results beyond summation order.  Defaults: {0, 2, 1, 0}. */
+typedef struct {
+    int32_t group_shift;  /* a work item gathers todo targets that share an octree cell of edge
+                             >= h / 2^group_shift (0..3)                                      */
+    int32_t cell_div;     /* candidate cells have an edge >= (query-box extent) / cell_div, so
+                             at most (cell_div + 1)^3 cells are looked up per item (1..3)     */
+    int32_t table_extra;  /* dense cell-table levels beyond one cell per particle (0..1); takes
+                             effect at the next sort                                          */
+    int32_t direct_pct;   /* FP32 pair loop: 0 evaluates every staged candidate directly
+                             (fastest measured); otherwise in-h pairs are queued per lane
+                             until more than this percentage of an item's first tests fall
+                             within h (1..101; 101 = always queue).  FP64 always queues.      */
+} sph_tuning;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
  * on the current CUDA device, with scratch for up to `capacity` particles (and up to
@@ -99,6 +117,10 @@ sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_str
 /* Replace the solve parameters of a context (precision, nngb, tol, max_iter, use_graph).
  * Changing box or periodic invalidates the sorted state (sph_sort must run again). */
 sph_status sph_set_params(sph_ctx *ctx, const sph_params *params);
+
+/* Read or replace the tuning of a context.  Errors: INVALID_ARG (NULL, out of range). */
+sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
+sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
 
 /* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix
  * sort, gather into a sorted SoA, cell tables).  pos_xyz_dev holds three planes of n

@@ -33,7 +33,7 @@ SPH_MAX_PASSES = 64
 
 EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sph_density_eval",
             "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error",
-            "sph_density_eval_static")
+            "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning")
 SPH_STATIC_MAX_PARTICLES = 32768
 
 
@@ -65,6 +65,9 @@ class SphStats(ctypes.Structure):
         ("density_ms", ctypes.c_double),
         ("density_launches", ctypes.c_int32),
         ("pad", ctypes.c_int32),
+        ("pair_tests", ctypes.c_int64),
+        ("pairs_per_pass", ctypes.c_int64 * SPH_MAX_PASSES),
+        ("density_ms_per_pass", ctypes.c_double * SPH_MAX_PASSES),
     ]
 
     def to_dict(self) -> dict:
@@ -80,7 +83,22 @@ class SphStats(ctypes.Structure):
             "solve_ms": float(self.solve_ms),
             "density_ms": float(self.density_ms),
             "density_launches": int(self.density_launches),
+            "pair_tests": int(self.pair_tests),
+            "pairs_per_pass": [int(v) for v in self.pairs_per_pass[: max(0, min(p, SPH_MAX_PASSES))]],
+            "density_ms_per_pass": [float(v) for v in self.density_ms_per_pass[: max(0, min(p, SPH_MAX_PASSES))]],
         }
+
+
+class SphTuning(ctypes.Structure):
+    _fields_ = [
+        ("group_shift", ctypes.c_int32),
+        ("cell_div", ctypes.c_int32),
+        ("table_extra", ctypes.c_int32),
+        ("direct_pct", ctypes.c_int32),
+    ]
+
+    def to_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 _lib = None
@@ -114,6 +132,10 @@ def lib() -> ctypes.CDLL:
     L.sph_status_string.argtypes = [i32]
     L.sph_last_error.restype = ctypes.c_char_p
     L.sph_last_error.argtypes = [vp]
+    L.sph_get_tuning.restype = i32
+    L.sph_get_tuning.argtypes = [vp, ctypes.POINTER(SphTuning)]
+    L.sph_set_tuning.restype = i32
+    L.sph_set_tuning.argtypes = [vp, ctypes.POINTER(SphTuning)]
     L.sph_density_eval_static.restype = i32
     L.sph_density_eval_static.argtypes = [ctypes.POINTER(SphParams), i64, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = L
@@ -145,6 +167,16 @@ def sph_create(params: SphParams, capacity: int, stream: int = 0):
     st = lib().sph_create(ctypes.byref(params), int(capacity), ctypes.c_void_p(stream or None),
                           ctypes.byref(out))
     return st, out.value
+
+
+def sph_get_tuning(ctx):
+    t = SphTuning()
+    st = lib().sph_get_tuning(ctypes.c_void_p(ctx), ctypes.byref(t))
+    return st, t
+
+
+def sph_set_tuning(ctx, tuning: SphTuning) -> int:
+    return lib().sph_set_tuning(ctypes.c_void_p(ctx), ctypes.byref(tuning))
 
 
 def sph_set_params(ctx, params: SphParams) -> int:
@@ -249,6 +281,18 @@ class Solver:
         if st not in ok:
             raise SphError(st, sph_last_error(self.ctx))
         return st
+
+    def tuning(self) -> dict:
+        st, t = sph_get_tuning(self.ctx)
+        self._check(st)
+        return t.to_dict()
+
+    def set_tuning(self, **kw):
+        st, t = sph_get_tuning(self.ctx)
+        self._check(st)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        self._check(sph_set_tuning(self.ctx, t))
 
     def set_params(self, **params):
         self.params = make_params(**params)

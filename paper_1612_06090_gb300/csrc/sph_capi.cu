@@ -55,10 +55,11 @@ struct sph_ctx {
 
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t dev_ev[2 * SPH_MAX_PASSES] = {};  // around each density launch
+    sph_tuning tuning{0, 2, 1, 0};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
     int grid_cap = 0;
-    int density_grid[2] = {0, 0};
+    int density_grid[3] = {0, 0, 0};  // FP64, FP32 with queue, FP32 direct
 };
 
 namespace {
@@ -121,7 +122,9 @@ size_t carve(sph_ctx *c, char *base)
     const int64_t cap = c->capacity;
     const int64_t hs = radix_hist_size(cap);
     const int64_t aux = scan_aux_size(std::max<int64_t>(cap, hs)) + 8;
-    const int64_t ctab_cap = 3 * cap + 2;
+    // periodic: 8^lc + 1 <= 8 n + 1 entries (one extra table level at most); batch groups:
+    // sum of (8^lc + 1) <= 8 n + groups
+    const int64_t ctab_cap = 8 * cap + c->max_groups + 2;
     const int64_t gcap = c->max_groups;
     size_t off = 0;
     auto take = [&](size_t bytes) -> void * {
@@ -172,6 +175,7 @@ SortArgs sort_args(sph_ctx *c)
     a.ds = c->ds;
     a.kl = c->kl;
     a.grid_cap = c->grid_cap;
+    a.table_extra = c->tuning.table_extra;
     a.launches = &c->launches;
     return a;
 }
@@ -203,18 +207,29 @@ SolveArgs solve_args(sph_ctx *c)
     a.ds = c->ds;
     a.grid_cap = c->grid_cap;
     a.precision = c->params.precision;
-    a.density_grid = c->density_grid[c->params.precision == SPH_PREC_FP64 ? 0 : 1];
+    a.density_grid = c->density_grid[c->params.precision == SPH_PREC_FP64 ? 0
+                                      : c->tuning.direct_pct == 0           ? 2
+                                                                            : 1];
     a.gmax = 32;
+    a.group_shift = c->tuning.group_shift;
+    a.cell_div = c->tuning.cell_div;
+    a.direct_pct = c->tuning.direct_pct;
     a.launches = &c->launches;
     return a;
 }
 
-// Level of the dense cell table: the finest level with at most one cell per particle.
-int table_level(int64_t n, int lmax)
+// Level of the dense cell table: the finest level with at most 8^extra cells per particle.
+int table_level(int64_t n, int lmax, int extra)
 {
     int lc = 0;
-    while (lc < lmax && lc < 10 && (1ll << (3 * (lc + 1))) <= n) lc++;
+    while (lc < lmax && lc < 10 && (1ll << (3 * (lc + 1))) <= (n << (3 * extra))) lc++;
     return lc;
+}
+
+bool tuning_ok(const sph_tuning *t)
+{
+    return t && t->group_shift >= 0 && t->group_shift <= 3 && t->cell_div >= 1 && t->cell_div <= 3 &&
+           t->table_extra >= 0 && t->table_extra <= 1 && t->direct_pct >= 0 && t->direct_pct <= 101;
 }
 
 sph_status read_state(sph_ctx *c)
@@ -276,13 +291,19 @@ sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *coun
         stats->unconverged = d.todo_count;
         stats->exceeded = d.exceeded;
         stats->pair_evals = (int64_t)d.pair_evals;
+        stats->pair_tests = (int64_t)d.pair_tests;
+        for (int k = 0; k < SPH_MAX_PASSES; k++)
+            stats->pairs_per_pass[k] = k < d.pass ? (int64_t)d.pairs_per_pass[k] : 0;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
         stats->solve_ms = ms;
         double dms = 0.0;
         for (int k = 0; k < passes_run; k++) {
             float m = 0.f;
-            if (cudaEventElapsedTime(&m, c->dev_ev[2 * k], c->dev_ev[2 * k + 1]) == cudaSuccess) dms += m;
+            if (cudaEventElapsedTime(&m, c->dev_ev[2 * k], c->dev_ev[2 * k + 1]) == cudaSuccess) {
+                dms += m;
+                stats->density_ms_per_pass[k] = m;
+            }
         }
         stats->density_ms = dms;
         stats->density_launches = passes_run;
@@ -355,10 +376,27 @@ sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_str
     for (int k = 0; k < 2 * SPH_MAX_PASSES; k++)
         if (cudaEventCreate(&c->dev_ev[k]) != cudaSuccess) return bail(SPH_ERR_CUDA);
     c->grid_cap = c->num_sms * 16;
-    c->density_grid[0] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP64);
-    c->density_grid[1] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN);
+    c->density_grid[0] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP64, 0);
+    c->density_grid[1] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN, 1);
+    c->density_grid[2] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN, 0);
     if (cudaMemset(c->ds, 0, sizeof(DevState)) != cudaSuccess) return bail(SPH_ERR_CUDA);
     *out = c;
+    return SPH_OK;
+}
+
+sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out)
+{
+    if (!ctx || !out) return SPH_ERR_INVALID_ARG;
+    *out = ctx->tuning;
+    return SPH_OK;
+}
+
+sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!tuning_ok(tuning)) return fail(ctx, SPH_ERR_INVALID_ARG, "tuning value out of range");
+    if (tuning->table_extra != ctx->tuning.table_extra) ctx->sorted = false;
+    ctx->tuning = *tuning;
     return SPH_OK;
 }
 
@@ -424,7 +462,7 @@ sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const do
     sg.tol = p.tol;
     sg.half_box = 0.5 * std::min(p.box[0], std::min(p.box[1], p.box[2]));
     sg.periodic = 1;
-    sg.level_c = table_level(n, ctx->kl.lmax);
+    sg.level_c = table_level(n, ctx->kl.lmax, ctx->tuning.table_extra);
     sg.tab_off = 0;
     sg.start = 0;
     sg.end = (int32_t)n;

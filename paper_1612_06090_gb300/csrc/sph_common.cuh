@@ -61,7 +61,10 @@ struct DevState {
     int32_t loop_flag;         // 1 while another pass is needed (device-side loop)
     int32_t pad0;
     unsigned long long pair_evals;  // in-h pairs accumulated over the solve
+    unsigned long long pair_tests;  // candidate-target distance tests (work done, not counted
+                                    // as algorithmic work)
     int32_t todo_per_pass[kMaxPasses];
+    unsigned long long pairs_per_pass[kMaxPasses];
 };
 
 enum DevStatusBits : int32_t {

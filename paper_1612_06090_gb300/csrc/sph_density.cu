@@ -30,8 +30,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kStage = 256;     // candidates staged per warp before a pair-loop flush
-constexpr int kMaxCells = 64;   // cells per item (4 per dimension)
+constexpr int kStage = 256;            // candidates staged per warp before a pair-loop flush
+constexpr int kStageCap = kStage + 32; // + room to pad the stage to a multiple of 32
+constexpr int kRing = 32;              // per-lane queue of in-h pairs (power of two)
+constexpr int kSubSteps = 16;          // tests per lane between drains (<= kRing / 2)
+constexpr int kMaxCells = 64;          // cells per item (4 per dimension)
 constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ float sqrt_approx(float x)
@@ -88,14 +91,20 @@ struct ItemGeom {
     uint32_t X0[3];   // fixed-point position of the first target
     int64_t lo[3];    // query box relative to X0, inclusive
     int64_t hi[3];
+    int qlo[3];       // the same bounds clamped to int32 (whole range for full dimensions),
+    int qhi[3];       // which is all the per-candidate test needs
+    int bmin[3];      // bounding box of the item's targets relative to X0
+    int bmax[3];
+    double hmax;      // largest h of the item's targets
     int full[3];      // periodic dimension covered entirely
     int level;        // enumeration level
     uint32_t c_lo[3]; // first cell per dimension
     int nc[3];        // cells per dimension
 };
 
-__device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl, bool active,
-                                           const uint4 &P, double hd, ItemGeom &G, int rel[3])
+__device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl, int cell_div,
+                                           bool active, const uint4 &P, double hd, ItemGeom &G,
+                                           int rel[3])
 {
     const uint32_t pc[3] = {P.x, P.y, P.z};
     double hmax = active ? hd : 0.0;
@@ -110,6 +119,8 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
         rel[d] = (int32_t)(pc[d] - G.X0[d]);
         const int bmin = __reduce_min_sync(kFull, active ? rel[d] : INT_MAX);
         const int bmax = __reduce_max_sync(kFull, active ? rel[d] : INT_MIN);
+        G.bmin[d] = bmin;
+        G.bmax[d] = bmax;
         const int64_t H = (int64_t)fmin(ceil(hmax * S.inv_q[d]) + 2.0, 4.0e18);
         G.lo[d] = (int64_t)bmin - H;
         G.hi[d] = (int64_t)bmax + H;
@@ -118,9 +129,13 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
         G.full[d] = S.periodic && (G.hi[d] - G.lo[d] + 1 >= range / 2);
         const int64_t ext = G.full[d] ? range : G.hi[d] - G.lo[d] + 1;
         E = ext > E ? ext : E;
+        G.qlo[d] = G.full[d] ? INT_MIN : (int)(G.lo[d] < INT_MIN ? (int64_t)INT_MIN : G.lo[d]);
+        G.qhi[d] = G.full[d] ? INT_MAX : (int)(G.hi[d] > INT_MAX ? (int64_t)INT_MAX : G.hi[d]);
     }
+    G.hmax = hmax;
+    // cells of at least E / cell_div: at most cell_div + 1 cells per dimension meet the query
     int l = kl.lmax;
-    while (l > 0 && 3 * (1ll << (cb - l)) < E) l--;
+    while (l > 0 && cell_div * (1ll << (cb - l)) < E) l--;
     if (S.periodic && l == 0) l = 1;  // keep shifts below 32; the level-1 cells cover the box
     G.level = l;
     const int s = cb - l;
@@ -178,48 +193,48 @@ __device__ __forceinline__ bool in_query(const ItemGeom &G, const uint4 &Pj, int
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         rj[d] = (int32_t)(pc[d] - G.X0[d]);
-        in = in && (G.full[d] || ((int64_t)rj[d] >= G.lo[d] && (int64_t)rj[d] <= G.hi[d]));
+        in = in && rj[d] >= G.qlo[d] && rj[d] <= G.qhi[d];
     }
     return in;
 }
 
 struct Acc32 {
-    float s_mw, c_mw, s_w, c_w, s_dw, c_dw;
+    float s_mw, c_mw, s_w, c_w, s_dw, c_dw;  // compensated totals
+    float p_mw, p_w, p_dw;                   // plain partial sums since the last merge
     int count;
 };
 
-// FP32 pair loop: lanes are targets, candidates are broadcast from shared memory.
-__device__ __forceinline__ void flush_f32(const float4 *__restrict__ stage, int cnt, float tx,
-                                          float ty, float tz, float h2f, float hinv2, Acc32 &A)
+__device__ __forceinline__ void merge32(Acc32 &A)
 {
-    for (int j0 = 0; j0 < cnt; j0 += 32) {
-        const int j1 = j0 + 32 < cnt ? j0 + 32 : cnt;
-        float pmw = 0.f, pw = 0.f, pdw = 0.f;
-        int pc = 0;
-        for (int j = j0; j < j1; j++) {
-            const float4 c = stage[j];
-            const float dx = c.x - tx, dy = c.y - ty, dz = c.z - tz;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < h2f) {
-                // M4 as a B-spline: w = 2 (1-q)^3 - 8 max(0, 1/2-q)^3,
-                // -q w' = 6 q ((1-q)^2 - 4 max(0, 1/2-q)^2)
-                const float q = sqrt_approx(r2 * hinv2);
-                const float a = 1.f - q;
-                const float b = fmaxf(0.5f - q, 0.f);
-                const float a2 = a * a, b2 = b * b;
-                const float w = fmaf(2.f * a, a2, -8.f * b * b2);
-                const float dw = 6.f * q * fmaf(-4.f, b2, a2);
-                pmw = fmaf(c.w, w, pmw);
-                pw += w;
-                pdw += dw;
-                pc++;
-            }
-        }
-        kahan_add(A.s_mw, A.c_mw, pmw);
-        kahan_add(A.s_w, A.c_w, pw);
-        kahan_add(A.s_dw, A.c_dw, pdw);
-        A.count += pc;
-    }
+    kahan_add(A.s_mw, A.c_mw, A.p_mw);
+    kahan_add(A.s_w, A.c_w, A.p_w);
+    kahan_add(A.s_dw, A.c_dw, A.p_dw);
+    A.p_mw = A.p_w = A.p_dw = 0.f;
+}
+
+// The M4 shape as a B-spline with u = max(1-q, 0) and v = max(1-2q, 0):
+//   w = 2 u^3 - v^3,   -q w' = 6 q (u^2 - v^2),
+// both zero for q >= 1, with no branch on q.  The sums carry w/2 and -q w'/6; the factors
+// 2 and 6 are applied once per target.
+__device__ __forceinline__ void m4_half(float q, float &w_half, float &dw_sixth)
+{
+    const float u = fmaxf(1.f - q, 0.f);
+    const float v = fmaxf(fmaf(-2.f, q, 1.f), 0.f);
+    const float u2 = u * u, v2 = v * v;
+    w_half = fmaf(-0.5f * v, v2, u2 * u);
+    dw_sixth = q * (u2 - v2);
+}
+
+// One in-h pair in FP32 from its squared distance and the neighbour mass.
+__device__ __forceinline__ void pair32(float2 e, float hinv2, Acc32 &A)
+{
+    const float q = sqrt_approx(e.x * hinv2);
+    float w, dw;
+    m4_half(q, w, dw);
+    A.p_mw = fmaf(e.y, w, A.p_mw);
+    A.p_w += w;
+    A.p_dw += dw;
+    A.count++;
 }
 
 // ---- FP64 pair terms, written as the FP64 reference writes them --------------------------
@@ -259,51 +274,158 @@ struct Acc64 {
     int count;
 };
 
-__device__ __forceinline__ void flush_f64(const float4 *__restrict__ stage,
-                                          const int *__restrict__ sidx, int cnt, float tx, float ty,
-                                          float tz, float h2loose, const double4_32a &ti, double h,
-                                          double h2, const SegInfo &S,
-                                          const double4_32a *__restrict__ pdbl, Acc64 &A)
+__device__ __forceinline__ void pair64(const double4_32a &ti, const double4_32a &cj, double h,
+                                       double h2, const SegInfo &S, Acc64 &A)
 {
-    for (int j = 0; j < cnt; j++) {
-        const float4 c = stage[j];
-        const float dxf = c.x - tx, dyf = c.y - ty, dzf = c.z - tz;
-        const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
-        if (r2f < h2loose) {
-            const double4_32a cj = pdbl[sidx[j]];
-            double dx = __dsub_rn(cj.x, ti.x);
-            double dy = __dsub_rn(cj.y, ti.y);
-            double dz = __dsub_rn(cj.z, ti.z);
-            if (S.periodic) {
-                dx = min_image64(dx, S.box[0]);
-                dy = min_image64(dy, S.box[1]);
-                dz = min_image64(dz, S.box[2]);
-            }
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                        __dmul_rn(dz, dz));
-            if (r2 < h2) {
-                const double q = __ddiv_rn(__dsqrt_rn(r2), h);
-                const double w = w64(q);
-                A.s_mw = __dadd_rn(A.s_mw, __dmul_rn(cj.w, w));
-                A.s_w = __dadd_rn(A.s_w, w);
-                A.s_dw = __dadd_rn(A.s_dw, mqdw64(q));
-                A.count++;
-            }
-        }
+    double dx = __dsub_rn(cj.x, ti.x);
+    double dy = __dsub_rn(cj.y, ti.y);
+    double dz = __dsub_rn(cj.z, ti.z);
+    if (S.periodic) {
+        dx = min_image64(dx, S.box[0]);
+        dy = min_image64(dy, S.box[1]);
+        dz = min_image64(dz, S.box[2]);
+    }
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (r2 < h2) {
+        const double q = __ddiv_rn(__dsqrt_rn(r2), h);
+        const double w = w64(q);
+        A.s_mw = __dadd_rn(A.s_mw, __dmul_rn(cj.w, w));
+        A.s_w = __dadd_rn(A.s_w, w);
+        A.s_dw = __dadd_rn(A.s_dw, mqdw64(q));
+        A.count++;
     }
 }
 
-template <bool kF64>
-__global__ void __launch_bounds__(kThreads, 2) k_density(SolveArgs a, const int32_t *__restrict__ todo)
+// Per-lane geometry of the pair loop: lane = (target t, slice s); the lane tests staged
+// candidates s, s + slices, s + 2 slices, ... against target t.
+struct LaneTarget {
+    float tx, ty, tz;  // target offset from the item origin
+    float h2;          // h^2 for the test (FP64 path: widened radius); -1 for idle lanes
+    float hinv2;
+    int slices, s;
+};
+
+// Test all staged candidates, queue the in-h ones per lane (ring of kRing entries), and
+// evaluate them in warp-wide rounds.  Only rounds in which every lane has a queued pair run
+// while testing continues; lanes drain their own backlog once it could overflow, and at
+// the end.  This keeps the long pair body on (nearly) full warps however unevenly the
+// in-h pairs fall across the targets.
+// kMode: 0 = FP64 (queue), 1 = FP32 with the queue until the in-h share is known, 2 = FP32
+// evaluated directly (no queue, no ring memory).
+template <int kMode>
+__device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__restrict__ sidx,
+                                      void *__restrict__ ring_raw, int cnt, int direct_pct,
+                                      const LaneTarget &L,
+                                      Acc32 &A32, Acc64 &A64, const double4_32a &ti, double h,
+                                      double h2, const SegInfo &S,
+                                      const double4_32a *__restrict__ pdbl)
 {
-    __shared__ float4 stage_all[kWarps][kStage];
-    __shared__ int sidx_all[kF64 ? kWarps : 1][kF64 ? kStage : 1];
+    constexpr bool kF64 = kMode == 0;
+    constexpr bool kQueue = kMode != 2;
+    const int lane = lane_id();
+    // pad to a multiple of 32 with candidates that are never within h
+    const int pad = (cnt + 31) & ~31;
+    for (int j = cnt + lane; j < pad; j += 32) stage[j] = make_float4(3e18f, 3e18f, 3e18f, 0.f);
+    __syncwarp();
+    float2(*ring32)[32] = (float2(*)[32])ring_raw;
+    int(*ring64)[32] = (int(*)[32])ring_raw;
+    auto drain_one = [&](int &head) {
+        if (kF64) {
+            const int j = ring64[head & (kRing - 1)][lane];
+            pair64(ti, pdbl[sidx[j]], h, h2, S, A64);
+        } else {
+            pair32(ring32[head & (kRing - 1)][lane], L.hinv2, A32);
+        }
+        head++;
+    };
+    const int steps = pad / L.slices;
+    int head = 0, tail = 0;
+    bool direct = !kQueue;
+    int k0 = 0;
+    for (; kQueue && k0 < steps && !direct; k0 += kSubSteps) {
+        const int k1 = k0 + kSubSteps < steps ? k0 + kSubSteps : steps;
+#pragma unroll 4
+        for (int k = k0; k < k1; k++) {
+            const int j = k * L.slices + L.s;
+            const float4 c = stage[j];
+            const float dx = c.x - L.tx, dy = c.y - L.ty, dz = c.z - L.tz;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < L.h2) {
+                if (kF64) ring64[tail & (kRing - 1)][lane] = j;
+                else ring32[tail & (kRing - 1)][lane] = make_float2(r2, c.w);
+                tail++;
+            }
+        }
+        // idle lanes never queue anything, so they do not hold the full rounds back
+        if (!kF64 && k0 == 0 && k1 == kSubSteps) {
+            // most of the first tests were in h: the remaining candidates are evaluated
+            // directly (the test and the pair body on all lanes, no queue)
+            const int queued = __reduce_add_sync(kFull, L.h2 >= 0.f ? tail : 0);
+            const int lanes = __popc(__ballot_sync(kFull, L.h2 >= 0.f));
+            direct = direct_pct == 0 || queued * 100 > direct_pct * lanes * kSubSteps;
+        }
+        const int full = __reduce_min_sync(kFull, L.h2 >= 0.f ? tail - head : INT_MAX);
+        // a lane only ever reads ring entries it wrote itself (idle lanes have none)
+        for (int r = 0; r < full; r++)
+            if (tail - head > 0) drain_one(head);
+        const int mx = __reduce_max_sync(kFull, tail - head);
+        for (int r = kRing - kSubSteps; r < mx; r++)
+            if (tail - head > kRing - kSubSteps) drain_one(head);
+        if (!kF64) merge32(A32);
+    }
+    if (kQueue) {
+        const int mx = __reduce_max_sync(kFull, tail - head);
+        for (int r = 0; r < mx; r++)
+            if (tail - head > 0) drain_one(head);
+        if (!kF64) merge32(A32);
+    }
+    if (!kF64 && direct) {
+        for (int kb = k0; kb < steps; kb += 32) {
+            const int ke = kb + 32 < steps ? kb + 32 : steps;
+#pragma unroll 4
+            for (int k = kb; k < ke; k++) {
+                const float4 c = stage[k * L.slices + L.s];
+                const float dx = c.x - L.tx, dy = c.y - L.ty, dz = c.z - L.tz;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                // the pair body runs under the test: a step in which no lane is within h
+                // costs only the test
+                if (r2 < L.h2) {
+                    const float q = sqrt_approx(r2 * L.hinv2);
+                    float w, dw;
+                    m4_half(q, w, dw);
+                    A32.p_mw = fmaf(c.w, w, A32.p_mw);
+                    A32.p_w += w;
+                    A32.p_dw += dw;
+                    A32.count++;
+                }
+            }
+            merge32(A32);
+        }
+    }
+    __syncwarp();
+}
+
+template <int kMode>
+__host__ __device__ constexpr int warp_smem_bytes()
+{
+    return kStageCap * 16 + (kMode == 0 ? kStageCap * 4 + kRing * 32 * 4 : kMode == 1 ? kRing * 32 * 8 : 0);
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
+    k_density(SolveArgs a, const int32_t *__restrict__ todo)
+{
+    constexpr bool kF64 = kMode == 0;
+    extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4 *stage = stage_all[warp];
-    int *sidx = sidx_all[kF64 ? warp : 0];
+    unsigned char *wbase = smem + (size_t)warp * warp_smem_bytes<kMode>();
+    float4 *stage = (float4 *)wbase;
+    int *sidx = (int *)(wbase + kStageCap * 16);
+    void *ring = wbase + kStageCap * 16 + (kF64 ? kStageCap * 4 : 0);
     const int n_items = a.ds->n_items;
     const int todo_count = a.ds->todo_count;
-    unsigned long long pairs = 0;
+    const int pass = a.ds->pass;
+    unsigned long long pairs = 0, tests = 0;
 
     for (;;) {
         int it = 0;
@@ -312,92 +434,139 @@ __global__ void __launch_bounds__(kThreads, 2) k_density(SolveArgs a, const int3
         if (it >= n_items) break;
         const int t0 = a.items[it];
         const int t1 = it + 1 < n_items ? a.items[it + 1] : todo_count;
-        const bool active = lane < t1 - t0;
-        const int p = todo[active ? t0 + lane : t0];
+        const int G = t1 - t0;
+        int Gp = 1;
+        while (Gp < G) Gp <<= 1;
+        LaneTarget L;
+        L.slices = 32 / Gp;
+        const int t = lane & (Gp - 1);
+        L.s = lane / Gp;
+        const bool active = t < G;
+        const int p = todo[t0 + (active ? t : 0)];
         const uint4 P = a.pfix[p];
         const double hd = a.h[p];
         const int g = a.kl.seg_bits > 0 ? (int)(a.key[p] >> (3 * a.kl.lmax)) : 0;
         const SegInfo &S = a.segs[g];
 
-        ItemGeom G;
+        ItemGeom G3;
         int rel[3];
-        item_setup(S, a.kl, active, P, hd, G, rel);
+        item_setup(S, a.kl, a.cell_div, active, P, hd, G3, rel);
         const float qf[3] = {(float)S.q[0], (float)S.q[1], (float)S.q[2]};
-        const float tx = (float)rel[0] * qf[0];
-        const float ty = (float)rel[1] * qf[1];
-        const float tz = (float)rel[2] * qf[2];
+        L.tx = (float)rel[0] * qf[0];
+        L.ty = (float)rel[1] * qf[1];
+        L.tz = (float)rel[2] * qf[2];
         const float hf = (float)hd;
-        const float h2f = hf * hf;
-        const float hinv2 = 1.0f / h2f;
-        // FP64 path: widened radius for the pre-filter (rounding of the FP32 offsets and the
-        // fixed-point quantisation both stay far inside the margin)
-        const double qmax = fmax(S.q[0], fmax(S.q[1], S.q[2]));
-        const float hl = (float)(hd * (1.0 + 1e-4) + 4.0 * qmax);
-        const float h2loose = hl * hl;
+        L.hinv2 = 1.0f / (hf * hf);
         double4_32a ti = make_double4_32a(0, 0, 0, 0);
-        if (kF64) ti = a.pdbl[p];
+        if (kF64) {
+            // widened pre-filter radius: the FP32 offsets and the fixed-point quantisation both
+            // stay far inside the margin; the exact FP64 test decides
+            const double qmax = fmax(S.q[0], fmax(S.q[1], S.q[2]));
+            const float hl = (float)(hd * (1.0 + 1e-4) + 4.0 * qmax);
+            L.h2 = active ? hl * hl : -1.f;
+            ti = a.pdbl[p];
+        } else {
+            L.h2 = active ? hf * hf : -1.f;
+        }
 
-        const int ncell = G.nc[0] * G.nc[1] * G.nc[2];
+        const int ncell = G3.nc[0] * G3.nc[1] * G3.nc[2];
         if (ncell > kMaxCells) {  // cannot happen by construction; report, never overrun
             if (lane == 0) atomicOr(&a.ds->status, 8);
             continue;
         }
         long long rr[2];
-        item_ranges(G, g, S, a.kl, a.ctab, a.key, ncell, rr);
+        item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, rr);
 
-        Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        // A candidate can lie within h of some target only inside the ball around the
+        // centre of the targets' box of radius (half-diagonal + h_max); staging keeps the
+        // box test (exact, integer) and adds this ball test (FP32 with a margin that covers
+        // the rounding of the offsets and the fixed-point quantisation).
+        float ccx, ccy, ccz, ball2;
+        {
+            const double qm = fmax(S.q[0], fmax(S.q[1], S.q[2]));
+            double hx[3], half2 = 0.0;
+            for (int d = 0; d < 3; d++) {
+                hx[d] = 0.5 * ((double)G3.bmax[d] - (double)G3.bmin[d]) * S.q[d];
+                half2 += hx[d] * hx[d];
+            }
+            ccx = (float)(0.5 * ((double)G3.bmin[0] + (double)G3.bmax[0]) * S.q[0]);
+            ccy = (float)(0.5 * ((double)G3.bmin[1] + (double)G3.bmax[1]) * S.q[1]);
+            ccz = (float)(0.5 * ((double)G3.bmin[2] + (double)G3.bmax[2]) * S.q[2]);
+            const double R = sqrt(half2) + G3.hmax;
+            const double Rm = R * (1.0 + 1e-5) + 8.0 * qm;
+            ball2 = (float)(Rm * Rm);
+        }
+
+        Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
         Acc64 A64 = {0.0, 0.0, 0.0, 0};
         int cnt = 0;
+        int staged = 0;
         for (int c = 0; c < ncell; c++) {
             const long long rc = __shfl_sync(kFull, (c < 32) ? rr[0] : rr[1], c & 31);
-            const int2 r = make_int2((int)(rc & 0xffffffffll), (int)(rc >> 32));
-            for (int base = r.x; base < r.y; base += 32) {
-                const int j = base + lane;
-                int rj[3] = {0, 0, 0};
-                uint4 Pj = make_uint4(0, 0, 0, 0);
-                bool in = false;
-                if (j < r.y) {
-                    Pj = a.pfix[j];
-                    in = in_query(G, Pj, rj);
-                }
-                const unsigned m = __ballot_sync(kFull, in);
-                if (in) {
-                    const int slot = cnt + __popc(m & lanemask_lt());
-                    stage[slot] = make_float4((float)rj[0] * qf[0], (float)rj[1] * qf[1],
-                                              (float)rj[2] * qf[2], __uint_as_float(Pj.w));
-                    if (kF64) sidx[slot] = j;
-                }
-                cnt += __popc(m);
-                if (cnt > kStage - 32) {
-                    __syncwarp();
-                    if (kF64) flush_f64(stage, sidx, cnt, tx, ty, tz, h2loose, ti, hd, hd * hd, S, a.pdbl, A64);
-                    else flush_f32(stage, cnt, tx, ty, tz, h2f, hinv2, A32);
-                    __syncwarp();
-                    cnt = 0;
+            const int rbeg = (int)(rc & 0xffffffffll), rend = (int)(rc >> 32);
+            for (int base = rbeg; base < rend; base += 64) {
+                // two independent 16-byte loads per lane before either is used
+                const int j0 = base + lane, j1 = base + 32 + lane;
+                uint4 P0 = make_uint4(0, 0, 0, 0), P1 = make_uint4(0, 0, 0, 0);
+                if (j0 < rend) P0 = a.pfix[j0];
+                if (j1 < rend) P1 = a.pfix[j1];
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    const int j = half ? j1 : j0;
+                    const uint4 &Pj = half ? P1 : P0;
+                    int rj[3] = {0, 0, 0};
+                    bool in = j < rend && in_query(G3, Pj, rj);
+                    float fx = 0.f, fy = 0.f, fz = 0.f;
+                    if (in) {
+                        fx = (float)rj[0] * qf[0];
+                        fy = (float)rj[1] * qf[1];
+                        fz = (float)rj[2] * qf[2];
+                        const float ex = fx - ccx, ey = fy - ccy, ez = fz - ccz;
+                        in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= ball2;
+                    }
+                    const unsigned m = __ballot_sync(kFull, in);
+                    if (in) {
+                        const int slot = cnt + __popc(m & lanemask_lt());
+                        stage[slot] = make_float4(fx, fy, fz, __uint_as_float(Pj.w));
+                        if (kF64) sidx[slot] = j;
+                    }
+                    cnt += __popc(m);
+                    if (cnt > kStage - 32) {
+                        __syncwarp();
+                        flush<kMode>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+                        staged += cnt;
+                        cnt = 0;
+                    }
                 }
             }
         }
         __syncwarp();
         if (cnt > 0) {
-            if (kF64) flush_f64(stage, sidx, cnt, tx, ty, tz, h2loose, ti, hd, hd * hd, S, a.pdbl, A64);
-            else flush_f32(stage, cnt, tx, ty, tz, h2f, hinv2, A32);
+            flush<kMode>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+            staged += cnt;
         }
-        __syncwarp();
 
-        if (active) {
-            double smw, sw, sdw;
-            int count;
-            if (kF64) {
-                smw = A64.s_mw;
-                sw = A64.s_w;
-                sdw = A64.s_dw;
-                count = A64.count;
-            } else {
-                smw = (double)A32.s_mw - (double)A32.c_mw;
-                sw = (double)A32.s_w - (double)A32.c_w;
-                sdw = (double)A32.s_dw - (double)A32.c_dw;
-                count = A32.count;
-            }
+        // combine the slices of each target (FP64 sums across lanes)
+        double smw, sw, sdw;
+        int count;
+        if (kF64) {
+            smw = A64.s_mw;
+            sw = A64.s_w;
+            sdw = A64.s_dw;
+            count = A64.count;
+        } else {
+            smw = 2.0 * ((double)A32.s_mw - (double)A32.c_mw);
+            sw = 2.0 * ((double)A32.s_w - (double)A32.c_w);
+            sdw = 6.0 * ((double)A32.s_dw - (double)A32.c_dw);
+            count = A32.count;
+        }
+        for (int o = Gp; o < 32; o <<= 1) {
+            smw += __shfl_xor_sync(kFull, smw, o);
+            sw += __shfl_xor_sync(kFull, sw, o);
+            sdw += __shfl_xor_sync(kFull, sdw, o);
+            count += __shfl_xor_sync(kFull, count, o);
+        }
+        if (active && L.s == 0) {
             const double h = hd;
             a.e_h[p] = h;
             a.e_rho[p] = smw * (8.0 / (kPi * h * h * h));
@@ -406,27 +575,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_density(SolveArgs a, const int3
             a.e_cnt[p] = count;
             pairs += (unsigned long long)count;
         }
+        if (lane == 0) tests += (unsigned long long)staged * (unsigned long long)G;
     }
     pairs = warp_sum(pairs);
-    if (lane == 0 && pairs) atomicAdd(&a.ds->pair_evals, pairs);
+    if (lane == 0) {
+        if (pairs) {
+            atomicAdd(&a.ds->pair_evals, pairs);
+            if (pass < kMaxPasses) atomicAdd(&a.ds->pairs_per_pass[pass], pairs);
+        }
+        if (tests) atomicAdd(&a.ds->pair_tests, tests);
+    }
 }
 
 }  // namespace
 
-int density_blocks_per_sm(int precision)
+template <int kMode>
+int blocks_per_sm()
 {
+    const int bytes = kWarps * warp_smem_bytes<kMode>();
+    cudaFuncSetAttribute(k_density<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int b = 0;
-    if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<true>, kThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<kMode>, kThreads, bytes);
     return b > 0 ? b : 1;
+}
+
+int mode_of(int precision, int direct_pct) { return precision == 0 ? 0 : direct_pct == 0 ? 2 : 1; }
+
+int density_blocks_per_sm(int precision, int direct_pct)
+{
+    switch (mode_of(precision, direct_pct)) {
+    case 0: return blocks_per_sm<0>();
+    case 1: return blocks_per_sm<1>();
+    default: return blocks_per_sm<2>();
+    }
 }
 
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
-    if (a.precision == 0) k_density<true><<<a.density_grid, kThreads, 0, st>>>(a, todo);
-    else k_density<false><<<a.density_grid, kThreads, 0, st>>>(a, todo);
+    switch (mode_of(a.precision, a.direct_pct)) {
+    case 0:
+        k_density<0><<<a.density_grid, kThreads, kWarps * warp_smem_bytes<0>(), st>>>(a, todo);
+        break;
+    case 1:
+        k_density<1><<<a.density_grid, kThreads, kWarps * warp_smem_bytes<1>(), st>>>(a, todo);
+        break;
+    default:
+        k_density<2><<<a.density_grid, kThreads, kWarps * warp_smem_bytes<2>(), st>>>(a, todo);
+        break;
+    }
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }

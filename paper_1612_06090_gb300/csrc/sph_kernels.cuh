@@ -19,6 +19,7 @@ struct SortArgs {
     DevState *ds;
     KeyLayout kl;
     int grid_cap;          // upper bound on blocks per launch
+    int table_extra;       // dense-table levels beyond one cell per particle (batch groups)
     int *launches;         // host-side launch counter
 };
 
@@ -63,6 +64,10 @@ struct SolveArgs {
     int grid_cap;
     int density_grid;          // persistent blocks of the density kernels
     int gmax;                  // targets per work item (<= 32)
+    int group_shift;           // items group targets sharing an octree cell of edge >= h / 2^shift
+    int cell_div;              // candidate cells have an edge >= (query extent) / cell_div
+    int direct_pct;            // in-h percentage of the first tests above which the pair loop
+                               // evaluates directly instead of queueing (101 = always queue)
     int precision;             // sph_precision
     int *launches;
     cudaEvent_t dens_ev[2];    // optional events recorded around the density launch
@@ -77,6 +82,6 @@ cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, i
 
 // sph_density.cu
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st);
-int density_blocks_per_sm(int precision);
+int density_blocks_per_sm(int precision, int direct_pct);
 
 }  // namespace sph

@@ -22,18 +22,20 @@ __device__ __forceinline__ int seg_of(uint64_t k, const KeyLayout &kl)
     return kl.seg_bits > 0 ? (int)(k >> (3 * kl.lmax)) : 0;
 }
 
-// Grouping level of a target: the finest octree level whose cell edge is at least h.
+// Grouping level of a target: the finest octree level whose cell edge is at least
+// h / 2^shift (so the targets of one work item lie within about h of each other).
 // `big` marks targets whose cell plus h reaches half the periodic range; those form
 // single-target work items so every staged offset is a minimum-image offset.
 __device__ __forceinline__ void bucket_of(uint64_t k, double h, const SegInfo &S,
-                                          const KeyLayout &kl, int &lvl, uint64_t &prefix,
-                                          bool &big)
+                                          const KeyLayout &kl, int shift, int &lvl,
+                                          uint64_t &prefix, bool &big)
 {
     const int cb = kl.coord_bits;
     const double maxinv = fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
     const double hu = ceil(h * maxinv);
+    const double edge = ceil(ldexp(h * maxinv, -shift));
     int l = kl.lmax;
-    while (l > 0 && (double)(1ll << (cb - l)) < hu) l--;
+    while (l > 0 && (double)(1ll << (cb - l)) < edge) l--;
     lvl = l;
     prefix = k >> (3 * (kl.lmax - l));
     big = S.periodic && ((double)(1ll << (cb - l)) + hu >= (double)(1ll << (cb - 1)));
@@ -66,7 +68,11 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
         a.ds->max_iter = max_iter;
         a.ds->loop_flag = n > 0 ? 1 : 0;
         a.ds->pair_evals = 0ull;
-        for (int k = 0; k < kMaxPasses; k++) a.ds->todo_per_pass[k] = 0;
+        a.ds->pair_tests = 0ull;
+        for (int k = 0; k < kMaxPasses; k++) {
+            a.ds->todo_per_pass[k] = 0;
+            a.ds->pairs_per_pass[k] = 0ull;
+        }
     }
 }
 
@@ -96,7 +102,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
         int l;
         uint64_t pre;
         bool big;
-        bucket_of(k, a.h[p], a.segs[seg_of(k, a.kl)], a.kl, l, pre, big);
+        bucket_of(k, a.h[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big);
         int head = (t % a.gmax == 0) || big;
         if (!head) {
             const int pp = todo[t - 1];
@@ -104,7 +110,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
             int lp;
             uint64_t prep;
             bool bigp;
-            bucket_of(kp, a.h[pp], a.segs[seg_of(kp, a.kl)], a.kl, lp, prep, bigp);
+            bucket_of(kp, a.h[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp);
             head = bigp || lp != l || prep != pre;
         }
         a.flags[t] = head;

@@ -127,8 +127,8 @@ sph_status setup_current_device(DeviceSetup **out)
             scan_aux_size(kHistEntries > kMaxN ? kHistEntries : kMaxN) + 8 > kAuxEntries)
             return SPH_ERR_UNSUPPORTED;
         s.base = (unsigned char *)ptr;
-        s.density_grid[0] = s.num_sms * density_blocks_per_sm(SPH_PREC_FP64);
-        s.density_grid[1] = s.num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN);
+        s.density_grid[0] = s.num_sms * density_blocks_per_sm(SPH_PREC_FP64, 0);
+        s.density_grid[1] = s.num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN, 0);
         s.done = true;
     }
     *out = &s;
@@ -208,6 +208,7 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     sa.ds = c.ds;
     sa.kl = kl;
     sa.grid_cap = dev->num_sms * 16;
+    sa.table_extra = 0;
     sa.launches = &launches;
     CUS(launch_keys_periodic(sa, n, pos_xyz_dev, mass_dev, sg, params->box, st));
     int which = 0;
@@ -242,6 +243,9 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     a.precision = params->precision;
     a.density_grid = dev->density_grid[params->precision == SPH_PREC_FP64 ? 0 : 1];
     a.gmax = 32;
+    a.group_shift = 1;
+    a.cell_div = 3;
+    a.direct_pct = 0;
     a.launches = &launches;
     CUS(launch_solve_init(a, h_dev, 1, st));
     CUS(launch_pass(a, 0, false, st));
