@@ -55,6 +55,18 @@ struct sph_ctx {
 
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t dev_ev[2 * SPH_MAX_PASSES] = {};  // around each density launch
+
+    // CUDA graph of the pass loop (a conditional while node whose body runs two passes)
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture the body
+    cudaGraph_t loop_graph = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    int body_kernels = 0;               // kernels per body execution
+    struct {
+        int64_t n = -1;
+        int which = -1, precision = -1, grid = -1;
+        sph_tuning tuning{};
+        KeyLayout kl{};
+    } graph_key;
     sph_tuning tuning{0, 2, 1, 0};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
@@ -250,40 +262,116 @@ sph_status device_status_error(sph_ctx *c, int bits)
     return fail(c, SPH_ERR_DEVICE_STATUS, "device flagged the input:%s", what.c_str());
 }
 
+void drop_graph(sph_ctx *c)
+{
+    if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+    if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
+    c->loop_exec = nullptr;
+    c->loop_graph = nullptr;
+    c->graph_key.n = -1;
+}
+
+// Executable graph of the pass loop: a conditional while node whose body runs two passes
+// (todo list 0 -> 1, then 1 -> 0) and sets the loop condition on the device, so the loop
+// needs no host round trip per pass.  Rebuilt only when the launch arguments change.
+sph_status loop_graph(sph_ctx *c, const SolveArgs &a0)
+{
+    const bool same = c->graph_key.n == c->n && c->graph_key.which == c->which &&
+                      c->graph_key.precision == a0.precision && c->graph_key.grid == a0.density_grid &&
+                      memcmp(&c->graph_key.tuning, &c->tuning, sizeof(sph_tuning)) == 0 &&
+                      memcmp(&c->graph_key.kl, &c->kl, sizeof(KeyLayout)) == 0 && c->loop_exec;
+    if (same) return SPH_OK;
+    drop_graph(c);
+    SolveArgs a = a0;
+    a.dens_ev[0] = a.dens_ev[1] = nullptr;
+    int launches = 0;
+    a.launches = &launches;
+    cudaGraph_t g = nullptr;
+    CU(c, cudaGraphCreate(&g, 0), "creating the loop graph");
+    c->loop_graph = g;
+    cudaGraphConditionalHandle handle;
+    CU(c, cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault), "loop condition");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = handle;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(c, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p), "conditional node");
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    CU(c, cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal),
+       "capturing the loop body");
+    cudaError_t e1 = launch_pass(a, 0, true, c->cap_stream);
+    cudaError_t e2 = launch_pass(a, 1, true, c->cap_stream);
+    cudaError_t e3 = launch_set_loop(handle, c->ds, c->cap_stream);
+    cudaError_t e4 = cudaStreamEndCapture(c->cap_stream, &body);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(c);
+        return cuda_fail(c, e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4,
+                         "capturing the loop body");
+    }
+    CU(c, cudaGraphInstantiate(&c->loop_exec, g, 0), "instantiating the loop graph");
+    c->body_kernels = launches + 1;
+    c->graph_key.n = c->n;
+    c->graph_key.which = c->which;
+    c->graph_key.precision = a0.precision;
+    c->graph_key.grid = a0.density_grid;
+    c->graph_key.tuning = c->tuning;
+    c->graph_key.kl = c->kl;
+    return SPH_OK;
+}
+
 // The pass loop shared by sph_density_solve and sph_batch_solve.
 sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *count_out,
                      double *nw_out, sph_stats *stats)
 {
     cudaStream_t st = c->stream;
+    const bool graph = c->params.use_graph != 0;
     const int launches0 = c->launches;
     SolveArgs a = solve_args(c);
+    sph_status s = SPH_OK;
+    if (graph) {
+        s = loop_graph(c, a);
+        if (s != SPH_OK) return s;
+    }
     CU(c, cudaEventRecord(c->ev[2], st), "event");
-    CU(c, cudaMemsetAsync(c->ds, 0, sizeof(DevState), st), "clearing the device state");
+    CU(c, cudaMemsetAsync(&c->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
     CU(c, launch_solve_init(a, h_inout, c->params.max_iter, st), "solve init");
-    sph_status s = read_state(c);
-    if (s != SPH_OK) return s;
-    if (c->ds_host->status) return device_status_error(c, c->ds_host->status);
+    if (!graph) {
+        s = read_state(c);
+        if (s != SPH_OK) return s;
+        if (c->ds_host->status | c->ds_host->sort_status)
+            return device_status_error(c, c->ds_host->status | c->ds_host->sort_status);
+    }
 
-    int cur = 0;
     int passes_run = 0;
-    for (int pass = 0; pass < c->params.max_iter; pass++) {
-        a.dens_ev[0] = c->dev_ev[2 * pass];
-        a.dens_ev[1] = c->dev_ev[2 * pass + 1];
-        CU(c, launch_pass(a, cur, true, st), "density pass");
-        passes_run = pass + 1;
-        CU(c, cudaMemcpyAsync(&c->ds_host->todo_count, &c->ds->todo_count, sizeof(int32_t),
-                              cudaMemcpyDeviceToHost, st),
-           "reading the todo count");
-        CU(c, cudaStreamSynchronize(st), "synchronising the pass");
-        cur = 1 - cur;
-        if (c->ds_host->todo_count == 0) break;
+    if (graph) {
+        CU(c, cudaGraphLaunch(c->loop_exec, st), "launching the loop graph");
+    } else {
+        int cur = 0;
+        for (int pass = 0; pass < c->params.max_iter; pass++) {
+            a.dens_ev[0] = c->dev_ev[2 * pass];
+            a.dens_ev[1] = c->dev_ev[2 * pass + 1];
+            CU(c, launch_pass(a, cur, true, st), "density pass");
+            passes_run = pass + 1;
+            CU(c, cudaMemcpyAsync(&c->ds_host->todo_count, &c->ds->todo_count, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st),
+               "reading the todo count");
+            CU(c, cudaStreamSynchronize(st), "synchronising the pass");
+            cur = 1 - cur;
+            if (c->ds_host->todo_count == 0) break;
+        }
     }
     CU(c, launch_scatter(a, h_inout, rho_out, count_out, nw_out, nullptr, st), "scatter");
     CU(c, cudaEventRecord(c->ev[3], st), "event");
     s = read_state(c);
     if (s != SPH_OK) return s;
     const DevState &d = *c->ds_host;
-    if (d.status) return device_status_error(c, d.status);
+    // the while body (two passes) ran ceil(passes / 2) times
+    if (graph) c->launches += (d.pass > 0 ? (d.pass + 1) / 2 : 1) * c->body_kernels;
+    if (d.status | d.sort_status) return device_status_error(c, d.status | d.sort_status);
     if (stats) {
         stats->passes = d.pass;
         stats->kernel_launches = c->launches - launches0 + c->sort_launches;
@@ -375,6 +463,8 @@ sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_str
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(SPH_ERR_CUDA);
     for (int k = 0; k < 2 * SPH_MAX_PASSES; k++)
         if (cudaEventCreate(&c->dev_ev[k]) != cudaSuccess) return bail(SPH_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(SPH_ERR_CUDA);
     c->grid_cap = c->num_sms * 16;
     c->density_grid[0] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP64, 0);
     c->density_grid[1] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN, 1);
@@ -428,6 +518,8 @@ void sph_destroy(sph_ctx *ctx)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     for (int k = 0; k < 2 * SPH_MAX_PASSES; k++)
         if (ctx->dev_ev[k]) cudaEventDestroy(ctx->dev_ev[k]);
+    drop_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 
@@ -481,9 +573,13 @@ sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const do
     CU(ctx, launch_cell_table(a, n, ctx->key[which], st), "cell table");
     CU(ctx, cudaEventRecord(ctx->ev[1], st), "event");
     ctx->sort_launches = ctx->launches - launches0;
-    sph_status s = read_state(ctx);
-    if (s != SPH_OK) return s;
-    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    if (!ctx->params.use_graph) {
+        // without graphs the sort reports bad input itself; with graphs it stays
+        // asynchronous and the solve reports it
+        sph_status s = read_state(ctx);
+        if (s != SPH_OK) return s;
+        if (ctx->ds_host->sort_status) return device_status_error(ctx, ctx->ds_host->sort_status);
+    }
     ctx->sorted = true;
     return SPH_OK;
 }
@@ -521,11 +617,12 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
     if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
     cudaStream_t st = ctx->stream;
     SolveArgs a = solve_args(ctx);
-    CU(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), st), "clearing the device state");
+    CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
     CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
     sph_status s = read_state(ctx);
     if (s != SPH_OK) return s;
-    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    if (ctx->ds_host->status | ctx->ds_host->sort_status)
+        return device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
     CU(ctx, launch_pass(a, 0, false, st), "density pass");
     CU(ctx, launch_scatter(a, nullptr, rho_out_dev, count_out_dev, nw_out_dev, dnw_out_dev, st), "scatter");
     s = read_state(ctx);
@@ -585,9 +682,12 @@ sph_status sph_batch_solve(sph_ctx *ctx, int64_t n_groups, const int64_t *offset
     CU(ctx, launch_cell_table(a, n, ctx->key[which], st), "cell table");
     CU(ctx, cudaEventRecord(ctx->ev[1], st), "event");
     ctx->sort_launches = ctx->launches - launches0;
-    sph_status s = read_state(ctx);
-    if (s != SPH_OK) return s;
-    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    sph_status s = SPH_OK;
+    if (!ctx->params.use_graph) {
+        s = read_state(ctx);
+        if (s != SPH_OK) return s;
+        if (ctx->ds_host->sort_status) return device_status_error(ctx, ctx->ds_host->sort_status);
+    }
     s = run_solve(ctx, h_inout_dev, rho_out_dev, count_out_dev, nw_out_dev, stats);
     if (stats) {
         float ms = 0.f;

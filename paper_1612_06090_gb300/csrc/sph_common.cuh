@@ -59,7 +59,9 @@ struct DevState {
     int32_t pass;              // passes completed
     int32_t max_iter;          // pass limit
     int32_t loop_flag;         // 1 while another pass is needed (device-side loop)
-    int32_t pad0;
+    int32_t pass_count;        // entries this pass evaluates (0: the pass is skipped)
+    int32_t sort_status;       // input errors found by the sort (kept across solves)
+    int32_t pad1;
     unsigned long long pair_evals;  // in-h pairs accumulated over the solve
     unsigned long long pair_tests;  // candidate-target distance tests (work done, not counted
                                     // as algorithmic work)

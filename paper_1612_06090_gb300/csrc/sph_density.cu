@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
     int *sidx = (int *)(wbase + kStageCap * 16);
     void *ring = wbase + kStageCap * 16 + (kF64 ? kStageCap * 4 : 0);
     const int n_items = a.ds->n_items;
-    const int todo_count = a.ds->todo_count;
+    const int todo_count = a.ds->pass_count;
     const int pass = a.ds->pass;
     unsigned long long pairs = 0, tests = 0;
 

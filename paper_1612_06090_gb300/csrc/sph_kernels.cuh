@@ -77,6 +77,7 @@ cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_it
 // One evaluation pass over todo[cur]; when `update`, also the h update and the next todo
 // list (todo[1 - cur]).
 cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t st);
+cudaError_t launch_set_loop(cudaGraphConditionalHandle handle, const DevState *ds, cudaStream_t st);
 cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, int32_t *count_out,
                            double *nw_out, double *dnw_out, cudaStream_t st);
 

@@ -67,6 +67,7 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
         a.ds->pass = 0;
         a.ds->max_iter = max_iter;
         a.ds->loop_flag = n > 0 ? 1 : 0;
+        a.ds->pass_count = 0;
         a.ds->pair_evals = 0ull;
         a.ds->pair_tests = 0ull;
         for (int k = 0; k < kMaxPasses; k++) {
@@ -76,18 +77,30 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
     }
 }
 
+// A pass evaluates pass_count entries: the whole todo list while the loop runs, none once it
+// has converged or reached max_iter (so a pass queued after that is a no-op).
 __global__ void k_pass_begin(DevState *ds)
 {
     ds->item_head = 0;
     ds->todo_next = 0;
-    if (ds->pass < kMaxPasses) ds->todo_per_pass[ds->pass] = ds->todo_count;
+    const bool run = ds->todo_count > 0 && ds->pass < ds->max_iter;
+    ds->pass_count = run ? ds->todo_count : 0;
+    if (run && ds->pass < kMaxPasses) ds->todo_per_pass[ds->pass] = ds->todo_count;
 }
 
 __global__ void k_pass_end(DevState *ds)
 {
-    ds->todo_count = ds->todo_next;
-    ds->pass += 1;
+    if (ds->pass_count > 0) {
+        ds->todo_count = ds->todo_next;
+        ds->pass += 1;
+    }
     ds->loop_flag = (ds->todo_count > 0 && ds->pass < ds->max_iter) ? 1 : 0;
+}
+
+// Device-side loop condition of the CUDA-graph pass loop.
+__global__ void k_set_loop(cudaGraphConditionalHandle handle, const DevState *ds)
+{
+    cudaGraphSetConditional(handle, ds->loop_flag ? 1u : 0u);
 }
 
 // Work-item heads: a new item starts at every multiple of gmax, whenever the grouping
@@ -95,7 +108,7 @@ __global__ void k_pass_end(DevState *ds)
 // single-target ("big") entries.
 __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
 {
-    const int T = a.ds->todo_count;
+    const int T = a.ds->pass_count;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int p = todo[t];
         const uint64_t k = a.key[p];
@@ -121,7 +134,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
 // roundings spelled out so no product is fused into an FMA).
 __global__ void k_h_update(SolveArgs a, const int32_t *__restrict__ todo)
 {
-    const int T = a.ds->todo_count;
+    const int T = a.ds->pass_count;
     int exceeded = 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int p = todo[t];
@@ -200,7 +213,7 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
     k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
     if (a.launches) *a.launches += 2;
     // item starts = positions of the head flags
-    cudaError_t e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->todo_count,
+    cudaError_t e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->pass_count,
                                 &a.ds->n_items, a.scan_aux, a.grid_cap, st, a.launches);
     if (e != cudaSuccess) return e;
     if (a.dens_ev[0]) cudaEventRecord(a.dens_ev[0], st);
@@ -210,11 +223,17 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
     if (!update) return cudaGetLastError();
     k_h_update<<<grid, kThreads, 0, st>>>(a, todo);
     if (a.launches) *a.launches += 1;
-    e = compact_i32(a.flags, todo, a.todo[1 - cur], nullptr, a.n, &a.ds->todo_count, &a.ds->todo_next,
+    e = compact_i32(a.flags, todo, a.todo[1 - cur], nullptr, a.n, &a.ds->pass_count, &a.ds->todo_next,
                     a.scan_aux, a.grid_cap, st, a.launches);
     if (e != cudaSuccess) return e;
     k_pass_end<<<1, 1, 0, st>>>(a.ds);
     if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_loop(cudaGraphConditionalHandle handle, const DevState *ds, cudaStream_t st)
+{
+    k_set_loop<<<1, 1, 0, st>>>(handle, ds);
     return cudaGetLastError();
 }
 

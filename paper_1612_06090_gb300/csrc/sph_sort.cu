@@ -60,7 +60,7 @@ __global__ void k_keys_periodic(int64_t n, const double *__restrict__ pos,
         key[i] = morton3(X >> shift, Y >> shift, Z >> shift);
         idx[i] = (int32_t)i;
     }
-    if (bad) atomicOr(&ds->status, bad);
+    if (bad) atomicOr(&ds->sort_status, bad);
 }
 
 // Group of particle i from the offsets (binary search: last g with offsets[g] <= i).
@@ -98,7 +98,7 @@ __global__ void k_keys_open(int64_t n, const double *__restrict__ pos,
         key[i] = k;
         idx[i] = (int32_t)i;
     }
-    if (bad) atomicOr(&ds->status, bad);
+    if (bad) atomicOr(&ds->sort_status, bad);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -299,7 +299,7 @@ __global__ void k_group_setup(int64_t n_groups, const int64_t *__restrict__ offs
             si.pad = 0;
             segs[g] = si;
             tsize[g] = (int32_t)((1ll << (3 * lc)) + 1);
-            if (!(si.nngb > 32.0 / 3.0) || !(si.tol >= 0.0) || e < s) atomicOr(&ds->status, kBadH);
+            if (!(si.nngb > 32.0 / 3.0) || !(si.tol >= 0.0) || e < s) atomicOr(&ds->sort_status, kBadH);
         }
         __syncthreads();
     }

@@ -255,6 +255,6 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     DevState host{};
     CUS(cudaMemcpyAsync(&host, c.ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     CUS(cudaStreamSynchronize(st));
-    if (host.status) return SPH_ERR_DEVICE_STATUS;
+    if (host.status | host.sort_status) return SPH_ERR_DEVICE_STATUS;
     return SPH_OK;
 }

@@ -289,3 +289,58 @@ def test_batch_matches_oracle(precision):
                                 box=(0, 0, 0), targets=m)
             assert np.all(np.abs(e["nw"] - 32.0) <= 1.0 + 1e-4)
             assert np.max(rel_err(g["rho"][s0 + m], e["rho"])) <= rtol
+
+
+# ---- the CUDA-graph pass loop ----------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_graph_loop_matches_host_loop(precision):
+    """use_graph=1 runs the same kernels in the same order from a device-side while loop:
+    results are bitwise those of the host-driven loop, on repeated solves and after a re-sort
+    to another particle count (the cached graph is rebuilt)."""
+    for n_override in (None, 3000):
+        wl = inputs.make("c1") if n_override is None else inputs.uniform_box(n=n_override, seed=44)
+        outs = []
+        for g in (0, 1):
+            s = B.Solver(4096, precision=precision, use_graph=bool(g))
+            s.sort(T(wl.pos), T(wl.mass))
+            r1 = s.solve(T(wl.h0))
+            r2 = s.solve(T(wl.h0))  # the cached graph again
+            torch.cuda.synchronize()
+            outs.append([{k: np_(v) for k, v in r.items() if torch.is_tensor(v)} | {"stats": r["stats"], "status": r["status"]}
+                         for r in (r1, r2)])
+            s.close()
+        for a, b in zip(outs[0], outs[1]):
+            assert a["status"] == b["status"] == B.SPH_OK
+            for k in ("h", "rho", "nw", "count"):
+                np.testing.assert_array_equal(a[k], b[k])
+            assert a["stats"]["passes"] == b["stats"]["passes"]
+            assert a["stats"]["todo_per_pass"] == b["stats"]["todo_per_pass"]
+            assert a["stats"]["pair_evals"] == b["stats"]["pair_evals"]
+
+
+def test_graph_loop_respects_max_iter():
+    pos = np.full((3, 100), 0.5)
+    for max_iter in (1, 4, 7):
+        s = B.Solver(100, precision=FP32, use_graph=True, max_iter=max_iter)
+        s.sort(T(pos), T(np.full(100, 0.01)))
+        r = s.solve(T(np.full(100, 0.1)))
+        torch.cuda.synchronize()
+        s.close()
+        assert r["status"] == B.SPH_ERR_NOT_CONVERGED
+        assert r["stats"]["passes"] == max_iter
+        h = 0.1
+        for _ in range(max_iter - 1):
+            h = h / 1.2599210498948732
+        assert np.all(np_(r["h"]) == h)
+
+
+def test_graph_mode_reports_bad_positions_at_solve():
+    s = B.Solver(100, precision=FP32, use_graph=True)
+    pos = np.random.default_rng(0).uniform(0, 1, (3, 100))
+    pos[0, 3] = np.inf
+    s.sort(T(pos), T(np.ones(100)))  # asynchronous in graph mode
+    with pytest.raises(B.SphError) as e:
+        s.solve(T(np.full(100, 0.1)))
+    assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    s.close()
