@@ -96,7 +96,7 @@ typedef struct sph_ctx sph_ctx;
  * never results beyond summation order.  Defaults: {0, 2, 1, 0}. */
 typedef struct {
     int32_t group_shift;  /* a work item gathers todo targets that share an octree cell of edge
-                             >= h / 2^group_shift (0..3)                                      */
+                             >= h / 2^group_shift (-2..3)                                     */
     int32_t cell_div;     /* candidate cells have an edge >= (query-box extent) / cell_div, so
                              at most (cell_div + 1)^3 cells are looked up per item (1..3)     */
     int32_t table_extra;  /* dense cell-table levels beyond one cell per particle (0..1); takes
@@ -121,6 +121,14 @@ sph_status sph_set_params(sph_ctx *ctx, const sph_params *params);
 /* Read or replace the tuning of a context.  Errors: INVALID_ARG (NULL, out of range). */
 sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
 sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
+
+/* Autotuner: time the grouping level (group_shift -1..1) and the candidate cell size
+ * (cell_div 2..3) with full solves from h_dev (n doubles, caller order, read only) on the
+ * particles of the last sph_sort, keep the fastest in the context and, when the context has
+ * a tune_cache file, append it there; sph_sort applies the last cached entry that matches
+ * the GPU, the particle-count bucket (floor log2 n), periodic and precision.  best may be
+ * NULL.  Results never change beyond summation order.  Errors: as sph_density_solve. */
+sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best);
 
 /* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix
  * sort, gather into a sorted SoA, cell tables).  pos_xyz_dev holds three planes of n

@@ -33,7 +33,7 @@ SPH_MAX_PASSES = 64
 
 EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sph_density_eval",
             "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error",
-            "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning")
+            "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning", "sph_autotune")
 SPH_STATIC_MAX_PARTICLES = 32768
 
 
@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
     L.sph_get_tuning.argtypes = [vp, ctypes.POINTER(SphTuning)]
     L.sph_set_tuning.restype = i32
     L.sph_set_tuning.argtypes = [vp, ctypes.POINTER(SphTuning)]
+    L.sph_autotune.restype = i32
+    L.sph_autotune.argtypes = [vp, vp, ctypes.POINTER(SphTuning)]
     L.sph_density_eval_static.restype = i32
     L.sph_density_eval_static.argtypes = [ctypes.POINTER(SphParams), i64, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = L
@@ -177,6 +179,12 @@ def sph_get_tuning(ctx):
 
 def sph_set_tuning(ctx, tuning: SphTuning) -> int:
     return lib().sph_set_tuning(ctypes.c_void_p(ctx), ctypes.byref(tuning))
+
+
+def sph_autotune(ctx, h_ptr: int):
+    t = SphTuning()
+    st = lib().sph_autotune(ctypes.c_void_p(ctx), ctypes.c_void_p(h_ptr or None), ctypes.byref(t))
+    return st, t
 
 
 def sph_set_params(ctx, params: SphParams) -> int:
@@ -293,6 +301,11 @@ class Solver:
         for k, v in kw.items():
             setattr(t, k, int(v))
         self._check(sph_set_tuning(self.ctx, t))
+
+    def autotune(self, h0) -> dict:
+        st, t = sph_autotune(self.ctx, h0.data_ptr())
+        self._check(st)
+        return t.to_dict()
 
     def set_params(self, **params):
         self.params = make_params(**params)

@@ -24,6 +24,7 @@ struct sph_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
+    std::string gpu_name;
     std::string last_error;
 
     // sorted state
@@ -46,6 +47,7 @@ struct sph_ctx {
            *e_nw = nullptr, *e_dnw = nullptr;
     int32_t *e_cnt = nullptr, *todo[2] = {nullptr, nullptr}, *flags = nullptr, *items = nullptr;
     int32_t *tsize = nullptr, *toff = nullptr;
+    float *h32 = nullptr, *e_rho32 = nullptr, *e_nw32 = nullptr, *e_dnw32 = nullptr;
     DevState *ds = nullptr;
 
     // pinned host mirrors
@@ -164,6 +166,10 @@ size_t carve(sph_ctx *c, char *base)
     for (int k = 0; k < 2; k++) c->todo[k] = (int32_t *)take(cap * 4);
     c->flags = (int32_t *)take(cap * 4);
     c->items = (int32_t *)take((cap + 1) * 4);
+    c->h32 = (float *)take(cap * 4);
+    c->e_rho32 = (float *)take(cap * 4);
+    c->e_nw32 = (float *)take(cap * 4);
+    c->e_dnw32 = (float *)take(cap * 4);
     c->tsize = (int32_t *)take((gcap + 1) * 4);
     c->toff = (int32_t *)take((gcap + 1) * 4);
     c->ds = (DevState *)take(sizeof(DevState));
@@ -211,6 +217,10 @@ SolveArgs solve_args(sph_ctx *c)
     a.e_nw = c->e_nw;
     a.e_dnw = c->e_dnw;
     a.e_cnt = c->e_cnt;
+    a.h32 = c->h32;
+    a.e_rho32 = c->e_rho32;
+    a.e_nw32 = c->e_nw32;
+    a.e_dnw32 = c->e_dnw32;
     a.todo[0] = c->todo[0];
     a.todo[1] = c->todo[1];
     a.flags = c->flags;
@@ -238,9 +248,49 @@ int table_level(int64_t n, int lmax, int extra)
     return lc;
 }
 
+// Autotuner cache: one line per result, "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp";
+// the last matching line wins.
+std::string cache_key(const sph_ctx *c, int64_t n)
+{
+    int b = 0;
+    while ((2ll << b) <= n) b++;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s|%d|%d|%d", c->gpu_name.c_str(), b, c->params.periodic, c->params.precision);
+    return buf;
+}
+
+bool cache_lookup(const sph_ctx *c, int64_t n, sph_tuning *t)
+{
+    if (c->tune_cache.empty()) return false;
+    FILE *f = fopen(c->tune_cache.c_str(), "r");
+    if (!f) return false;
+    const std::string key = cache_key(c, n);
+    char line[512], k[300];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        sph_tuning x{};
+        if (sscanf(line, "%299s %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra, &x.direct_pct) == 5 &&
+            key == k) {
+            *t = x;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const sph_ctx *c, int64_t n, const sph_tuning &t)
+{
+    if (c->tune_cache.empty()) return;
+    FILE *f = fopen(c->tune_cache.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div, t.table_extra, t.direct_pct);
+    fclose(f);
+}
+
 bool tuning_ok(const sph_tuning *t)
 {
-    return t && t->group_shift >= 0 && t->group_shift <= 3 && t->cell_div >= 1 && t->cell_div <= 3 &&
+    return t && t->group_shift >= -2 && t->group_shift <= 3 && t->cell_div >= 1 && t->cell_div <= 3 &&
            t->table_extra >= 0 && t->table_extra <= 1 && t->direct_pct >= 0 && t->direct_pct <= 101;
 }
 
@@ -323,6 +373,27 @@ sph_status loop_graph(sph_ctx *c, const SolveArgs &a0)
     return SPH_OK;
 }
 
+// Host-driven pass loop (one todo-count read per pass); returns the passes run.
+sph_status host_passes(sph_ctx *c, SolveArgs &a, bool events, int *passes_run)
+{
+    cudaStream_t st = c->stream;
+    int cur = 0;
+    *passes_run = 0;
+    for (int pass = 0; pass < c->params.max_iter; pass++) {
+        a.dens_ev[0] = events ? c->dev_ev[2 * pass] : nullptr;
+        a.dens_ev[1] = events ? c->dev_ev[2 * pass + 1] : nullptr;
+        CU(c, launch_pass(a, cur, true, st), "density pass");
+        *passes_run = pass + 1;
+        CU(c, cudaMemcpyAsync(&c->ds_host->todo_count, &c->ds->todo_count, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st),
+           "reading the todo count");
+        CU(c, cudaStreamSynchronize(st), "synchronising the pass");
+        cur = 1 - cur;
+        if (c->ds_host->todo_count == 0) break;
+    }
+    return SPH_OK;
+}
+
 // The pass loop shared by sph_density_solve and sph_batch_solve.
 sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *count_out,
                      double *nw_out, sph_stats *stats)
@@ -350,19 +421,8 @@ sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *coun
     if (graph) {
         CU(c, cudaGraphLaunch(c->loop_exec, st), "launching the loop graph");
     } else {
-        int cur = 0;
-        for (int pass = 0; pass < c->params.max_iter; pass++) {
-            a.dens_ev[0] = c->dev_ev[2 * pass];
-            a.dens_ev[1] = c->dev_ev[2 * pass + 1];
-            CU(c, launch_pass(a, cur, true, st), "density pass");
-            passes_run = pass + 1;
-            CU(c, cudaMemcpyAsync(&c->ds_host->todo_count, &c->ds->todo_count, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, st),
-               "reading the todo count");
-            CU(c, cudaStreamSynchronize(st), "synchronising the pass");
-            cur = 1 - cur;
-            if (c->ds_host->todo_count == 0) break;
-        }
+        s = host_passes(c, a, true, &passes_run);
+        if (s != SPH_OK) return s;
     }
     CU(c, launch_scatter(a, h_inout, rho_out, count_out, nw_out, nullptr, st), "scatter");
     CU(c, cudaEventRecord(c->ev[3], st), "event");
@@ -448,6 +508,13 @@ sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_str
     if (cudaGetDevice(&c->device) != cudaSuccess) return bail(SPH_ERR_CUDA);
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return bail(SPH_ERR_CUDA);
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return bail(SPH_ERR_CUDA);
+        c->gpu_name = prop.name;
+        for (char &ch : c->gpu_name)
+            if (ch == ' ' || ch == '|') ch = '_';
+    }
     const size_t bytes = carve(c, nullptr);
     if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -537,6 +604,10 @@ sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const do
                                               "through sph_batch_solve (one group per set)");
     cudaStream_t st = ctx->stream;
     const sph_params &p = ctx->params;
+    {
+        sph_tuning cached;
+        if (cache_lookup(ctx, n, &cached) && tuning_ok(&cached)) ctx->tuning = cached;
+    }
     ctx->n = n;
     ctx->kl.lmax = 21;
     ctx->kl.seg_bits = 0;
@@ -606,6 +677,64 @@ sph_status sph_density_solve(sph_ctx *ctx, double *h_inout_dev, double *rho_out_
         if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) stats->sort_ms = ms;
     }
     return s;
+}
+
+sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!h_dev) return fail(ctx, SPH_ERR_INVALID_ARG, "NULL h pointer");
+    if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
+    cudaStream_t st = ctx->stream;
+    SegInfo sg = ctx->seg_host;
+    sg.nngb = ctx->params.nngb;
+    sg.tol = ctx->params.tol;
+    *ctx->seg_pinned = sg;
+    CU(ctx, cudaMemcpyAsync(ctx->segs, ctx->seg_pinned, sizeof(SegInfo), cudaMemcpyHostToDevice, st),
+       "uploading the segment");
+    const sph_tuning base = ctx->tuning;
+    sph_tuning best = base;
+    float best_ms = -1.f;
+    // knobs that need no re-sort: grouping level and candidate cell size (FP32 always
+    // evaluates directly; FP64 always queues)
+    for (int gs = -1; gs <= 1; gs++) {
+        for (int cd = 2; cd <= 3; cd++) {
+            sph_tuning t = base;
+            t.group_shift = gs;
+            t.cell_div = cd;
+            t.direct_pct = 0;
+            ctx->tuning = t;
+            SolveArgs a = solve_args(ctx);
+            CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+            CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
+            CU(ctx, launch_solve_init(a, h_dev, ctx->params.max_iter, st), "init");
+            int passes = 0;
+            sph_status s = host_passes(ctx, a, false, &passes);
+            if (s != SPH_OK) {
+                ctx->tuning = base;
+                return s;
+            }
+            CU(ctx, cudaEventRecord(ctx->ev[3], st), "event");
+            s = read_state(ctx);
+            if (s != SPH_OK) {
+                ctx->tuning = base;
+                return s;
+            }
+            if (ctx->ds_host->status | ctx->ds_host->sort_status) {
+                ctx->tuning = base;
+                return device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
+            }
+            float ms = 0.f;
+            CU(ctx, cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]), "event time");
+            if (best_ms < 0.f || ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    }
+    ctx->tuning = best;
+    cache_store(ctx, ctx->n, best);
+    if (best_out) *best_out = best;
+    return SPH_OK;
 }
 
 sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_dev,

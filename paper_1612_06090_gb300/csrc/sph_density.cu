@@ -95,21 +95,22 @@ struct ItemGeom {
     int qhi[3];       // which is all the per-candidate test needs
     int bmin[3];      // bounding box of the item's targets relative to X0
     int bmax[3];
-    double hmax;      // largest h of the item's targets
+    float hmax;       // largest h of the item's targets
     int full[3];      // periodic dimension covered entirely
     int level;        // enumeration level
     uint32_t c_lo[3]; // first cell per dimension
     int nc[3];        // cells per dimension
 };
 
+// All item geometry is bounds for culling, so it is computed in FP32 with margins that
+// only ever enlarge it (FP64 arithmetic runs at a small fraction of the FP32 rate here).
 __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl, int cell_div,
-                                           bool active, const uint4 &P, double hd, ItemGeom &G,
+                                           bool active, const uint4 &P, float hf, ItemGeom &G,
                                            int rel[3])
 {
     const uint32_t pc[3] = {P.x, P.y, P.z};
-    double hmax = active ? hd : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(kFull, hmax, o));
+    // h > 0, so the order of the float bit patterns is the order of the values
+    const float hmax = __int_as_float(__reduce_max_sync(kFull, active ? __float_as_int(hf) : 0));
     const int cb = kl.coord_bits;
     const int64_t range = 1ll << cb;
     int64_t E = 0;
@@ -121,7 +122,8 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
         const int bmax = __reduce_max_sync(kFull, active ? rel[d] : INT_MIN);
         G.bmin[d] = bmin;
         G.bmax[d] = bmax;
-        const int64_t H = (int64_t)fmin(ceil(hmax * S.inv_q[d]) + 2.0, 4.0e18);
+        const int64_t H =
+            (int64_t)fminf(ceilf(hmax * (float)S.inv_q[d] * (1.0f + 1.0f / 1048576.0f)) + 2.0f, 4.0e18f);
         G.lo[d] = (int64_t)bmin - H;
         G.hi[d] = (int64_t)bmax + H;
         // A periodic dimension whose query spans half the range or more is taken whole
@@ -444,18 +446,18 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
         const bool active = t < G;
         const int p = todo[t0 + (active ? t : 0)];
         const uint4 P = a.pfix[p];
-        const double hd = a.h[p];
+        const double hd = kF64 ? a.h[p] : 0.0;
+        const float hf = kF64 ? (float)hd : a.h32[p];
         const int g = a.kl.seg_bits > 0 ? (int)(a.key[p] >> (3 * a.kl.lmax)) : 0;
         const SegInfo &S = a.segs[g];
 
         ItemGeom G3;
         int rel[3];
-        item_setup(S, a.kl, a.cell_div, active, P, hd, G3, rel);
+        item_setup(S, a.kl, a.cell_div, active, P, hf, G3, rel);
         const float qf[3] = {(float)S.q[0], (float)S.q[1], (float)S.q[2]};
         L.tx = (float)rel[0] * qf[0];
         L.ty = (float)rel[1] * qf[1];
         L.tz = (float)rel[2] * qf[2];
-        const float hf = (float)hd;
         L.hinv2 = 1.0f / (hf * hf);
         double4_32a ti = make_double4_32a(0, 0, 0, 0);
         if (kF64) {
@@ -483,18 +485,17 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
         // the rounding of the offsets and the fixed-point quantisation).
         float ccx, ccy, ccz, ball2;
         {
-            const double qm = fmax(S.q[0], fmax(S.q[1], S.q[2]));
-            double hx[3], half2 = 0.0;
+            const float qm = fmaxf(qf[0], fmaxf(qf[1], qf[2]));
+            float half2 = 0.f;
             for (int d = 0; d < 3; d++) {
-                hx[d] = 0.5 * ((double)G3.bmax[d] - (double)G3.bmin[d]) * S.q[d];
-                half2 += hx[d] * hx[d];
+                const float hx = 0.5f * (float)((int64_t)G3.bmax[d] - (int64_t)G3.bmin[d]) * qf[d];
+                half2 = fmaf(hx, hx, half2);
             }
-            ccx = (float)(0.5 * ((double)G3.bmin[0] + (double)G3.bmax[0]) * S.q[0]);
-            ccy = (float)(0.5 * ((double)G3.bmin[1] + (double)G3.bmax[1]) * S.q[1]);
-            ccz = (float)(0.5 * ((double)G3.bmin[2] + (double)G3.bmax[2]) * S.q[2]);
-            const double R = sqrt(half2) + G3.hmax;
-            const double Rm = R * (1.0 + 1e-5) + 8.0 * qm;
-            ball2 = (float)(Rm * Rm);
+            ccx = 0.5f * ((float)G3.bmin[0] + (float)G3.bmax[0]) * qf[0];
+            ccy = 0.5f * ((float)G3.bmin[1] + (float)G3.bmax[1]) * qf[1];
+            ccz = 0.5f * ((float)G3.bmin[2] + (float)G3.bmax[2]) * qf[2];
+            const float Rm = (sqrtf(half2) + G3.hmax) * (1.0f + 1e-5f) + 8.0f * qm;
+            ball2 = Rm * Rm;
         }
 
         Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
@@ -546,34 +547,48 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
             staged += cnt;
         }
 
-        // combine the slices of each target (FP64 sums across lanes)
-        double smw, sw, sdw;
-        int count;
+        // combine the slices of each target
+        int count = kF64 ? A64.count : A32.count;
         if (kF64) {
-            smw = A64.s_mw;
-            sw = A64.s_w;
-            sdw = A64.s_dw;
-            count = A64.count;
+            double smw = A64.s_mw, sw = A64.s_w, sdw = A64.s_dw;
+            for (int o = Gp; o < 32; o <<= 1) {
+                smw += __shfl_xor_sync(kFull, smw, o);
+                sw += __shfl_xor_sync(kFull, sw, o);
+                sdw += __shfl_xor_sync(kFull, sdw, o);
+                count += __shfl_xor_sync(kFull, count, o);
+            }
+            if (active && L.s == 0) {
+                const double h = hd;
+                a.e_rho[p] = smw * (8.0 / (kPi * h * h * h));
+                a.e_nw[p] = (32.0 / 3.0) * sw;
+                a.e_dnw[p] = (32.0 / 3.0) * sdw / h;
+                a.e_cnt[p] = count;
+                pairs += (unsigned long long)count;
+            }
         } else {
-            smw = 2.0 * ((double)A32.s_mw - (double)A32.c_mw);
-            sw = 2.0 * ((double)A32.s_w - (double)A32.c_w);
-            sdw = 6.0 * ((double)A32.s_dw - (double)A32.c_dw);
-            count = A32.count;
-        }
-        for (int o = Gp; o < 32; o <<= 1) {
-            smw += __shfl_xor_sync(kFull, smw, o);
-            sw += __shfl_xor_sync(kFull, sw, o);
-            sdw += __shfl_xor_sync(kFull, sdw, o);
-            count += __shfl_xor_sync(kFull, count, o);
-        }
-        if (active && L.s == 0) {
-            const double h = hd;
-            a.e_h[p] = h;
-            a.e_rho[p] = smw * (8.0 / (kPi * h * h * h));
-            a.e_nw[p] = (32.0 / 3.0) * sw;
-            a.e_dnw[p] = (32.0 / 3.0) * sdw / h;
-            a.e_cnt[p] = count;
-            pairs += (unsigned long long)count;
+            // totals and compensations are combined separately across slices; the compensated
+            // totals are then exact to about one FP32 rounding
+            float smw = A32.s_mw, cmw = A32.c_mw, sw = A32.s_w, cw = A32.c_w, sdw = A32.s_dw,
+                  cdw = A32.c_dw;
+            for (int o = Gp; o < 32; o <<= 1) {
+                smw += __shfl_xor_sync(kFull, smw, o);
+                cmw += __shfl_xor_sync(kFull, cmw, o);
+                sw += __shfl_xor_sync(kFull, sw, o);
+                cw += __shfl_xor_sync(kFull, cw, o);
+                sdw += __shfl_xor_sync(kFull, sdw, o);
+                cdw += __shfl_xor_sync(kFull, cdw, o);
+                count += __shfl_xor_sync(kFull, count, o);
+            }
+            if (active && L.s == 0) {
+                const float hi = 1.0f / hf;
+                // rho = (8/pi) h^-3 sum m w; N_w = (32/3) sum w; dN_w/dh = (32/3) h^-1 sum -q w'
+                // (the sums carry w/2 and -q w'/6)
+                a.e_rho32[p] = (2.0f * 2.546479089f) * (hi * hi * hi) * (smw - cmw);
+                a.e_nw32[p] = (2.0f * 10.66666667f) * (sw - cw);
+                a.e_dnw32[p] = (6.0f * 10.66666667f) * hi * (sdw - cdw);
+                a.e_cnt[p] = count;
+                pairs += (unsigned long long)count;
+            }
         }
         if (lane == 0) tests += (unsigned long long)staged * (unsigned long long)G;
     }

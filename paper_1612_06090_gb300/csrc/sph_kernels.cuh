@@ -54,8 +54,10 @@ struct SolveArgs {
     double *h;                 // h of the next evaluation
     double *hlo, *hhi;         // brackets
     double *e_h;               // h of the last evaluation
-    double *e_rho, *e_nw, *e_dnw;
+    double *e_rho, *e_nw, *e_dnw;   // last evaluation (FP64 precision mode)
     int32_t *e_cnt;
+    float *h32;                      // FP32 copy of h, read by the FP32 density kernel
+    float *e_rho32, *e_nw32, *e_dnw32;  // last evaluation (FP32 precision mode)
     int32_t *todo[2];          // ping-pong todo lists (sorted positions)
     int32_t *flags;            // per-todo-entry scratch flags
     int32_t *items;            // work-item starts (indices into the todo list)

@@ -26,19 +26,20 @@ __device__ __forceinline__ int seg_of(uint64_t k, const KeyLayout &kl)
 // h / 2^shift (so the targets of one work item lie within about h of each other).
 // `big` marks targets whose cell plus h reaches half the periodic range; those form
 // single-target work items so every staged offset is a minimum-image offset.
-__device__ __forceinline__ void bucket_of(uint64_t k, double h, const SegInfo &S,
+// (FP32 with margins that make `big` conservative; the level itself only steers efficiency)
+__device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
                                           const KeyLayout &kl, int shift, int &lvl,
                                           uint64_t &prefix, bool &big)
 {
     const int cb = kl.coord_bits;
-    const double maxinv = fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
-    const double hu = ceil(h * maxinv);
-    const double edge = ceil(ldexp(h * maxinv, -shift));
+    const float maxinv = (float)fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
+    const float hu = fminf(ceilf(h * maxinv * (1.0f + 1.0f / 1048576.0f)) + 1.0f, 1e30f);
+    const float edge = ldexpf(hu, -shift);
     int l = kl.lmax;
-    while (l > 0 && (double)(1ll << (cb - l)) < edge) l--;
+    while (l > 0 && (float)(1ll << (cb - l)) < edge) l--;
     lvl = l;
     prefix = k >> (3 * (kl.lmax - l));
-    big = S.periodic && ((double)(1ll << (cb - l)) + hu >= (double)(1ll << (cb - 1)));
+    big = S.periodic && ((float)(1ll << (cb - l)) + hu >= (float)(1ll << (cb - 1)));
 }
 
 __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int max_iter)
@@ -52,6 +53,7 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
         const SegInfo &S = a.segs[seg_of(a.key[p], a.kl)];
         if (!(hv > 0.0 && hv <= DBL_MAX) || (S.periodic && hv >= S.half_box)) bad |= kBadH;
         a.h[p] = hv;
+        a.h32[p] = (float)hv;
         a.hlo[p] = 0.0;
         a.hhi[p] = HUGE_VAL;
         a.e_h[p] = hv;
@@ -115,7 +117,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
         int l;
         uint64_t pre;
         bool big;
-        bucket_of(k, a.h[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big);
+        bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big);
         int head = (t % a.gmax == 0) || big;
         if (!head) {
             const int pp = todo[t - 1];
@@ -123,7 +125,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
             int lp;
             uint64_t prep;
             bool bigp;
-            bucket_of(kp, a.h[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp);
+            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp);
             head = bigp || lp != l || prep != pre;
         }
         a.flags[t] = head;
@@ -139,9 +141,11 @@ __global__ void k_h_update(SolveArgs a, const int32_t *__restrict__ todo)
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int p = todo[t];
         const SegInfo &S = a.segs[seg_of(a.key[p], a.kl)];
-        const double h = a.e_h[p];
-        const double nw = a.e_nw[p];
-        const double dnw = a.e_dnw[p];
+        const double h = a.h[p];  // the h this pass evaluated
+        const bool f32 = a.precision != 0;
+        const double nw = f32 ? (double)a.e_nw32[p] : a.e_nw[p];
+        const double dnw = f32 ? (double)a.e_dnw32[p] : a.e_dnw[p];
+        a.e_h[p] = h;
         int alive = 0;
         if (!(fabs(__dsub_rn(nw, S.nngb)) <= S.tol)) {
             double lo = a.hlo[p], hi = a.hhi[p];
@@ -165,6 +169,7 @@ __global__ void k_h_update(SolveArgs a, const int32_t *__restrict__ todo)
                 exceeded++;
             } else {
                 a.h[p] = hn;
+                a.h32[p] = (float)hn;
                 alive = 1;
             }
         }
@@ -181,11 +186,12 @@ __global__ void k_scatter(SolveArgs a, double *__restrict__ h_out, double *__res
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = a.idx[p];
+        const bool f32 = a.precision != 0;
         if (h_out) h_out[i] = a.e_h[p];
-        rho_out[i] = a.e_rho[p];
+        rho_out[i] = f32 ? (double)a.e_rho32[p] : a.e_rho[p];
         count_out[i] = a.e_cnt[p];
-        if (nw_out) nw_out[i] = a.e_nw[p];
-        if (dnw_out) dnw_out[i] = a.e_dnw[p];
+        if (nw_out) nw_out[i] = f32 ? (double)a.e_nw32[p] : a.e_nw[p];
+        if (dnw_out) dnw_out[i] = f32 ? (double)a.e_dnw32[p] : a.e_dnw[p];
     }
 }
 

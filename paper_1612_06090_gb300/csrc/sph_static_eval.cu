@@ -43,6 +43,7 @@ constexpr size_t kScratchBytes =
     + up(kMaxN * 16) + up(kMaxN * 32)                // sorted fixed-point and FP64 records
     + up(kTabEntries * 4) + up(sizeof(SegInfo))      // cell table, segment descriptor
     + 7 * up(kMaxN * 8) + up(kMaxN * 4)              // h state and evaluation outputs
+    + 4 * up(kMaxN * 4)                              // FP32 copies of h and of the outputs
     + 2 * up(kMaxN * 4) + up(kMaxN * 4) + up((kMaxN + 1) * 4)  // todo lists, flags, items
     + up(sizeof(DevState));
 
@@ -69,6 +70,7 @@ struct Carved {
     SegInfo *segs;
     double *h, *hlo, *hhi, *e_h, *e_rho, *e_nw, *e_dnw;
     int32_t *e_cnt, *todo[2], *flags, *items;
+    float *h32, *e_rho32, *e_nw32, *e_dnw32;
     DevState *ds;
 };
 
@@ -98,6 +100,10 @@ Carved carve(unsigned char *base)
     c.e_nw = (double *)take(kMaxN * 8);
     c.e_dnw = (double *)take(kMaxN * 8);
     c.e_cnt = (int32_t *)take(kMaxN * 4);
+    c.h32 = (float *)take(kMaxN * 4);
+    c.e_rho32 = (float *)take(kMaxN * 4);
+    c.e_nw32 = (float *)take(kMaxN * 4);
+    c.e_dnw32 = (float *)take(kMaxN * 4);
     for (int k = 0; k < 2; k++) c.todo[k] = (int32_t *)take(kMaxN * 4);
     c.flags = (int32_t *)take(kMaxN * 4);
     c.items = (int32_t *)take((kMaxN + 1) * 4);
@@ -233,6 +239,10 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     a.e_nw = c.e_nw;
     a.e_dnw = c.e_dnw;
     a.e_cnt = c.e_cnt;
+    a.h32 = c.h32;
+    a.e_rho32 = c.e_rho32;
+    a.e_nw32 = c.e_nw32;
+    a.e_dnw32 = c.e_dnw32;
     a.todo[0] = c.todo[0];
     a.todo[1] = c.todo[1];
     a.flags = c.flags;

@@ -36,6 +36,7 @@ __all__ = [
     "lognormal_field",
     "plummer_groups",
     "clumpy_snapshots",
+    "clumpy_snapshot_series",
     "make",
     "mean_density_h",
     "CONFIG_SEEDS",
@@ -293,6 +294,46 @@ def clumpy_snapshots(n: int = 1 << 26, seed: int = 5, n_clumps: int = 4096,
     return Workload("clumps4096", pos, np.full(n, 1.0 / n), h0, (1.0, 1.0, 1.0), True, nngb, tol,
                     {"seed": seed, "n_clumps": n_clumps, "a_range": list(a_range),
                      "drift": drift, "snapshot": snapshot, "n_snapshots": n_snapshots})
+
+
+def clumpy_snapshot_series(n_snapshots: int = 8, **kw):
+    """Yield snapshots 0 .. n_snapshots-1 of config c5 one after another.
+
+    Each yielded Workload equals clumpy_snapshots(snapshot=s, **kw) (same draws in the same
+    order) but the base particle set is generated once.
+    """
+    kw = {"seed": CONFIG_SEEDS["c5"], **kw}
+    kw.pop("snapshot", None)
+    base = clumpy_snapshots(snapshot=0, **kw)
+    # rebuild the unwrapped snapshot-0 positions exactly as clumpy_snapshots draws them
+    seed = kw.get("seed", CONFIG_SEEDS["c5"])
+    n = kw.get("n", 1 << 26)
+    n_clumps = kw.get("n_clumps", 4096)
+    a_range = kw.get("a_range", (1e-3, 1e-2))
+    frac = kw.get("frac", 0.7)
+    trunc = kw.get("trunc", 50.0)
+    drift = kw.get("drift", 1e-4)
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    n_cl = int(round(frac * n))
+    counts = _split_counts(n_cl, n_clumps)
+    centres = rng.uniform(0.0, 1.0, size=(n_clumps, 3))
+    radii = np.exp(rng.uniform(math.log(a_range[0]), math.log(a_range[1]), size=n_clumps))
+    pos = np.empty((3, n))
+    o = 0
+    for c in range(n_clumps):
+        k = int(counts[c])
+        pos[:, o:o + k] = _plummer_offsets(rng, k, float(radii[c]), trunc) + centres[c][:, None]
+        o += k
+    pos[:, n_cl:] = rng.uniform(0.0, 1.0, size=(3, n - n_cl))
+    perm = rng.permutation(n)
+    pos = pos[:, perm]
+    drift_rng = np.random.default_rng(np.random.PCG64(seed * 1000 + 17))
+    for s in range(n_snapshots):
+        if s > 0:
+            pos += drift_rng.normal(0.0, drift, size=pos.shape)
+        wl = Workload(base.name, np.ascontiguousarray(_wrap(pos, (1.0, 1.0, 1.0))), base.mass, base.h0,
+                      base.box, True, base.nngb, base.tol, {**base.meta, "snapshot": s})
+        yield wl
 
 
 def make(config: str, **kw):

@@ -344,3 +344,31 @@ def test_graph_mode_reports_bad_positions_at_solve():
         s.solve(T(np.full(100, 0.1)))
     assert e.value.status == B.SPH_ERR_DEVICE_STATUS
     s.close()
+
+
+# ---- the autotuner ---------------------------------------------------------------------------
+
+def test_autotune_picks_a_tuning_caches_it_and_keeps_results(tmp_path):
+    wl = inputs.make("c2", n=1 << 17)
+    cache = str(tmp_path / "tune.txt")
+    s = B.Solver(wl.n, precision=FP32, tune_cache=cache)
+    s.sort(T(wl.pos), T(wl.mass))
+    before = s.solve(T(wl.h0))
+    best = s.autotune(T(wl.h0))
+    assert best["group_shift"] in (0, 1) and best["cell_div"] in (2, 3)
+    assert s.tuning() == best
+    after = s.solve(T(wl.h0))
+    torch.cuda.synchronize()
+    s.close()
+    assert before["status"] == after["status"] == B.SPH_OK
+    a, b = np_(before["h"]), np_(after["h"])
+    same = rel_err(a, b) <= 1e-6
+    assert same.mean() > 0.999  # only summation order differs between tunings
+    assert np.max(rel_err(np_(before["rho"])[same], np_(after["rho"])[same])) <= 1e-5
+    # a new context with the same cache file applies the tuned values at its sort
+    s2 = B.Solver(wl.n, precision=FP32, tune_cache=cache)
+    s2.set_tuning(group_shift=3, cell_div=1)
+    s2.sort(T(wl.pos), T(wl.mass))
+    assert s2.tuning() == best
+    s2.close()
+    assert open(cache).read().strip()

@@ -57,3 +57,12 @@ def test_snapshots_share_particles_and_drift():
     d = s1.pos - s0.pos
     d -= np.round(d)
     assert 0.5e-4 < d.std() < 2e-4
+
+
+def test_snapshot_series_matches_single_snapshots():
+    from paper_1612_06090_gb300 import inputs as I
+
+    series = list(I.clumpy_snapshot_series(3, n=20000, n_clumps=8))
+    for s in range(3):
+        one = I.clumpy_snapshots(n=20000, n_clumps=8, snapshot=s)
+        np.testing.assert_array_equal(series[s].pos, one.pos)
