@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle targets (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -261,7 +262,8 @@ def run_native(args):
     # ---- FP32 + compensated: the headline ----
     s32 = make(B.SPH_PREC_FP32_KAHAN)
     s32._check(B.sph_sort(s32.ctx, n, pos.data_ptr(), mass.data_ptr()))
-    tuning = s32.autotune(h0)  # one-time per (GPU, size, precision); outside the timed region
+    # one-time per (GPU, size, precision); outside the timed region
+    tuning = s32.tuning() if args.no_autotune else s32.autotune(h0)
     with ClockSampler(local) as clk:
         ms32, st32, wall32 = timed(s32, args.steps, args.warmup)
     clocks = clk.summary()
@@ -283,9 +285,10 @@ def run_native(args):
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     achieved = pairs * FLOP_PER_PAIR / (dens_ms / 1e3) / 1e12 if dens_ms > 0 else 0.0
-    roof = {"bound": "alu", "kernel": "k_density<false> (FP32 pair loop)", "achieved": achieved,
+    roof = {"bound": "alu", "kernel": "k_density<2> (FP32 pair loop)", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": None,
+            "traffic": profiled_traffic() if args.config == "c2" and not args.n else None,
+            "traffic_note": "mean DRAM bytes per density launch (ncu, profiles/density_fp32_c2_1M.md)",
             "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
             "flop_per_pair": FLOP_PER_PAIR, "pairs_per_step": pairs // max(1, len(st32)),
             "density_ms_per_step": dens_ms / max(1, len(st32)),
@@ -384,6 +387,24 @@ def run_native(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def profiled_traffic():
+    """Mean DRAM bytes per density launch from the committed ncu summary, valid only while the
+    kernel sources are the ones that summary was captured from (else None)."""
+    import hashlib
+    import re
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", "density_fp32_c2_1M.md")).read()
+        src = b"".join(open(os.path.join(ROOT, "paper_1612_06090_gb300", "csrc", f), "rb").read()
+                       for f in ("sph_density.cu", "sph_common.cuh", "sph_kernels.cuh"))
+        want = re.search(r"kernel_source_sha256_16: (\w+)", text).group(1)
+        if hashlib.sha256(src).hexdigest()[:16] != want:
+            return None
+        return int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+    except Exception:
+        return None
 
 
 def roofline_from(stats_list, sms, sm_max_mhz, kernel):

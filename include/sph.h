@@ -93,7 +93,7 @@ typedef struct {
 typedef struct sph_ctx sph_ctx;
 
 /* Knobs of the spatial decomposition, set by the autotuner or by hand.  They change speed,
- * never results beyond summation order.  Defaults: {0, 2, 1, 0}. */
+ * never results beyond summation order.  Defaults: {0, 3, 1, 0}. */
 typedef struct {
     int32_t group_shift;  /* a work item gathers todo targets that share an octree cell of edge
                              >= h / 2^group_shift (-2..3)                                     */

@@ -69,7 +69,7 @@ struct sph_ctx {
         sph_tuning tuning{};
         KeyLayout kl{};
     } graph_key;
-    sph_tuning tuning{0, 2, 1, 0};
+    sph_tuning tuning{0, 3, 1, 0};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
     int grid_cap = 0;
