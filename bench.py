@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
+    ap.add_argument("--kernel", default="m4", choices=["m4", "c6"],
+                    help="c6: the paper's Wendland C6 kernel at Nngb = 295 +- 5")
     return ap.parse_args()
 
 
@@ -61,6 +63,8 @@ def workload(args):
     from paper_1612_06090_gb300 import inputs
 
     kw = {"n": args.n} if args.n else {}
+    if args.kernel == "c6":
+        kw.update(nngb=295.0, tol=5.0)
     wl = inputs.make(args.config, **kw)
     desc = {
         "c1": "uniform periodic box",
@@ -68,7 +72,8 @@ def workload(args):
         "c3": "log-normal density field (64^3 Gaussian, P(k)~k^-2, sigma_ln=2), periodic unit box",
         "c5": "4096 Plummer clumps (a log-uniform in [1e-3,1e-2], 70%) + background, periodic unit box",
     }[args.config]
-    return wl, f"{args.config}: {wl.n:,} particles, {desc}, Nngb={wl.nngb:g}+-{wl.tol:g}, M4 kernel"
+    kname = "Wendland C6 kernel" if args.kernel == "c6" else "M4 kernel"
+    return wl, f"{args.config}: {wl.n:,} particles, {desc}, Nngb={wl.nngb:g}+-{wl.tol:g}, {kname}"
 
 
 def dist_init(args):
@@ -154,7 +159,7 @@ class ClockSampler:
 
 # ---- the CPU oracle on a bounded sample --------------------------------------------------------
 
-def cpu_baseline(wl, n_targets):
+def cpu_baseline(wl, n_targets, kernel="m4"):
     import numpy as np
 
     import oracle
@@ -163,7 +168,7 @@ def cpu_baseline(wl, n_targets):
     tg = np.sort(rng.choice(wl.n, size=min(n_targets, wl.n), replace=False))
     t0 = time.perf_counter()
     r = oracle.solve(wl.pos, wl.mass, wl.h0[tg], box=wl.box, periodic=wl.periodic, nngb=wl.nngb,
-                     tol=wl.tol, targets=tg)
+                     tol=wl.tol, targets=tg, kernel="wendland_c6" if kernel == "c6" else "m4")
     dt = time.perf_counter() - t0
     return {"value": len(tg) / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{len(tg):,} random targets of the same workload solved against all "
@@ -179,11 +184,11 @@ def run_reference(args):
     wl, desc = workload(args)
     n_t = args.cpu_sample or max(1024, wl.n // 16)
     for _ in range(args.warmup):
-        cpu_baseline(wl, max(256, n_t // 8))
+        cpu_baseline(wl, max(256, n_t // 8), args.kernel)
     times = []
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(wl, n_t)
+        last = cpu_baseline(wl, n_t, args.kernel)
         times.append(last["seconds"])
     per_step = statistics.mean(times)
     value = min(n_t, wl.n) / per_step
@@ -225,7 +230,8 @@ def run_native(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def make(prec):
-        s = B.Solver(n, stream=stream, precision=prec, box=wl.box, nngb=wl.nngb, tol=wl.tol)
+        s = B.Solver(n, stream=stream, precision=prec, box=wl.box, nngb=wl.nngb, tol=wl.tol,
+                     kernel=B.SPH_KERNEL_WENDLAND_C6 if args.kernel == "c6" else B.SPH_KERNEL_M4)
         s.n = n  # sorted through the raw ABI below
         return s
 
@@ -359,7 +365,7 @@ def run_native(args):
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu and world == 1:
-        cpu = cpu_baseline(wl, args.cpu_sample or max(2048, n // 8))
+        cpu = cpu_baseline(wl, args.cpu_sample or max(2048, n // 8), args.kernel)
         cpu.pop("seconds", None)
         cpu.pop("passes", None)
 

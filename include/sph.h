@@ -61,8 +61,10 @@ typedef struct {
     double box[3];       /* periodic box lengths (> 0); ignored by sph_batch_solve        */
     int32_t periodic;    /* 1: periodic box, minimum image (positions in [0, box));
                             0: open boundaries                                          */
-    int32_t kernel;      /* sph_kernel; only SPH_KERNEL_M4 is implemented                 */
-    double nngb;         /* target weighted count (> 32/3, the self term)                 */
+    int32_t kernel;      /* sph_kernel: SPH_KERNEL_M4 (W = 8/(pi h^3) w) or
+                            SPH_KERNEL_WENDLAND_C6 (W = 1365/(64 pi h^3) (1-q)^8 (1+8q+25q^2+32q^3),
+                            the paper's kernel, Sec. II-B); sph_density_eval_static: M4 only */
+    double nngb;         /* target weighted count (> the self term: 32/3 M4, 1365/48 C6)   */
     double tol;          /* band half-width (>= 0)                                        */
     int32_t max_iter;    /* passes, 1..64                                                  */
     int32_t precision;   /* sph_precision                                                  */
@@ -111,7 +113,7 @@ typedef struct {
  * on the current CUDA device, with scratch for up to `capacity` particles (and up to
  * `capacity` batch groups).  Allocates all device memory the context will ever use.
  * Errors: INVALID_ARG (NULL params/out, capacity < 1 or > 2^31 - 2^20, bad params),
- * UNSUPPORTED (Wendland C6), CUDA (no device), OOM (device allocation failed). */
+ * CUDA (no device), OOM (device allocation failed). */
 sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_stream, sph_ctx **out);
 
 /* Replace the solve parameters of a context (precision, nngb, tol, max_iter, use_graph).

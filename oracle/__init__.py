@@ -9,6 +9,7 @@ marshals numpy arrays through ctypes.
 Functions
 ---------
 w(q), mqdw(q)                M4 shape w(q) and -q w'(q)          (Eq. 1 kernel)
+w_c6(q), mqdw_c6(q)          Wendland C6 shape (Sec. II-B kernel) and -q w'(q)
 evaluate(...)                one fixed-h density evaluation      (Eq. 1, Listing 1)
 solve(...)                   the h iteration on one particle set (Sec. IV-A, Listing 3)
 batch_solve(...)             the same over independent non-periodic groups
@@ -78,17 +79,21 @@ def _load():
     lib.oracle_w.argtypes = [ctypes.c_double]
     lib.oracle_mqdw.restype = ctypes.c_double
     lib.oracle_mqdw.argtypes = [ctypes.c_double]
+    lib.oracle_w_c6.restype = ctypes.c_double
+    lib.oracle_w_c6.argtypes = [ctypes.c_double]
+    lib.oracle_mqdw_c6.restype = ctypes.c_double
+    lib.oracle_mqdw_c6.argtypes = [ctypes.c_double]
     lib.oracle_eval.restype = ctypes.c_int
     lib.oracle_eval.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int64, ip,
-                                dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, ip, ip]
+                                dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, ip, ip, ctypes.c_int]
     lib.oracle_solve.restype = ctypes.c_int
     lib.oracle_solve.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int64, ip, ctypes.c_int, dp,
-                                 dp, dp, ip, i32p, ctypes.POINTER(OracleStats)]
+                                 dp, dp, ip, i32p, ctypes.POINTER(OracleStats), ctypes.c_int]
     lib.oracle_batch_solve.restype = ctypes.c_int
     lib.oracle_batch_solve.argtypes = [ctypes.c_int64, ip, dp, dp, dp, dp, dp, dp, ctypes.c_int,
                                        ctypes.c_int, dp, dp, dp, ip, i32p,
-                                       ctypes.POINTER(OracleStats)]
+                                       ctypes.POINTER(OracleStats), ctypes.c_int]
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     _lib = lib
@@ -126,11 +131,24 @@ def mqdw(q: float) -> float:
     return float(_load().oracle_mqdw(float(q)))
 
 
+def w_c6(q: float) -> float:
+    """Wendland C6 shape w(q); the kernel is W = 1365 / (64 pi h^3) w(r/h)."""
+    return float(_load().oracle_w_c6(float(q)))
+
+
+def mqdw_c6(q: float) -> float:
+    """-q w'(q) of the Wendland C6 shape; dN_w/dh = (1365/48)(1/h) sum_j mqdw_c6(q_j)."""
+    return float(_load().oracle_mqdw_c6(float(q)))
+
+
+KERNELS = {"m4": 0, "wendland_c6": 1}
+
+
 _MODES = {"grid": 0, "brute": 1}
 
 
 def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, mode="grid",
-             near_rel=0.0):
+             near_rel=0.0, kernel="m4"):
     """One density evaluation at fixed smoothing lengths.
 
     pos: (3, N); mass: (N,); h: one value per target (targets=None: all N particles).
@@ -152,7 +170,7 @@ def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, mod
     rc = lib.oracle_eval(n, _dp(x), _dp(y), _dp(z), _dp(mass), _dp(box), int(bool(periodic)),
                          nt if tg is not None else -1, _ip(tg) if tg is not None else None, _dp(h),
                          _MODES[mode], float(near_rel), _dp(rho), _dp(nw), _dp(dnw), _ip(count),
-                         _ip(near))
+                         _ip(near), KERNELS[kernel])
     if rc != 0:
         raise MemoryError("oracle_eval failed to allocate")
     out = {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
@@ -162,7 +180,7 @@ def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, mod
 
 
 def solve(pos, mass, h0, box=(1.0, 1.0, 1.0), periodic=True, nngb=64.0, tol=2.0, max_iter=64,
-          targets=None, mode="grid"):
+          targets=None, mode="grid", kernel="m4"):
     """Run the smoothing-length iteration for the targets (None: all particles).
 
     Every particle contributes as a neighbour; only the targets are solved (the density
@@ -186,13 +204,13 @@ def solve(pos, mass, h0, box=(1.0, 1.0, 1.0), periodic=True, nngb=64.0, tol=2.0,
     rc = lib.oracle_solve(n, _dp(x), _dp(y), _dp(z), _dp(mass), _dp(box), int(bool(periodic)),
                           float(nngb), float(tol), int(max_iter), nt if tg is not None else -1,
                           _ip(tg) if tg is not None else None, _MODES[mode], _dp(h), _dp(rho),
-                          _dp(nw), _ip(count), _i32p(status), ctypes.byref(st))
+                          _dp(nw), _ip(count), _i32p(status), ctypes.byref(st), KERNELS[kernel])
     if rc != 0:
         raise MemoryError("oracle_solve failed to allocate")
     return {"h": h, "rho": rho, "nw": nw, "count": count, "status": status, "stats": st.to_dict()}
 
 
-def batch_solve(offsets, pos, mass, h0, nngb, tol, max_iter=64, mode="grid"):
+def batch_solve(offsets, pos, mass, h0, nngb, tol, max_iter=64, mode="grid", kernel="m4"):
     """The iteration over independent non-periodic groups (group g = [offsets[g], offsets[g+1]))."""
     lib = _load()
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -210,7 +228,7 @@ def batch_solve(offsets, pos, mass, h0, nngb, tol, max_iter=64, mode="grid"):
     x, y, z = (np.ascontiguousarray(pos[d]) for d in range(3))
     rc = lib.oracle_batch_solve(g, _ip(offsets), _dp(x), _dp(y), _dp(z), _dp(mass), _dp(nngb),
                                 _dp(tol), int(max_iter), _MODES[mode], _dp(h), _dp(rho), _dp(nw),
-                                _ip(count), _i32p(status), ctypes.byref(st))
+                                _ip(count), _i32p(status), ctypes.byref(st), KERNELS[kernel])
     if rc != 0:
         raise MemoryError("oracle_batch_solve failed to allocate")
     return {"h": h, "rho": rho, "nw": nw, "count": count, "status": status, "stats": st.to_dict()}

@@ -12,7 +12,8 @@
  *    Read in gather form: the smoothing length of the target particle i is used for
  *    every pair (the printed equation carries h_j; see the readings list).
  *    The self pair j = i is included.  A neighbour is a particle with r_ij < h, strictly.
- *  - Kernel W: M4 cubic spline in 3-D with compact support h,
+ *  - Kernel W: M4 cubic spline in 3-D with compact support h (or the paper's Wendland C6,
+ *    selected by the `kernel` argument; see oracle_w_c6),
  *    W(r, h) = 8 / (pi h^3) w(q), q = r / h,
  *    w = 1 - 6 q^2 + 6 q^3 (q <= 1/2), 2 (1 - q)^3 (1/2 < q < 1), 0 otherwise.
  *    (The paper runs a Wendland C6 kernel with 295 neighbours, Sec. II-B; this solve
@@ -75,6 +76,35 @@ double oracle_w(double q)
     return 0.0;
 }
 
+/* Wendland C6 shape (the kernel of Sec. II-B, 295 neighbours) with compact support h:
+ * W(r, h) = 1365 / (64 pi h^3) w(q), w = (1 - q)^8 (1 + 8 q + 25 q^2 + 32 q^3) for q < 1. */
+double oracle_w_c6(double q)
+{
+    if (q < 1.0) {
+        double a = 1.0 - q;
+        double a2 = a * a;
+        double a4 = a2 * a2;
+        double a8 = a4 * a4;
+        double p = 1.0 + q * (8.0 + q * (25.0 + q * 32.0));
+        return a8 * p;
+    }
+    return 0.0;
+}
+
+/* -q w'(q) of the Wendland C6 shape: 22 q^2 (1 - q)^7 (1 + 7 q + 16 q^2). */
+double oracle_mqdw_c6(double q)
+{
+    if (q < 1.0) {
+        double a = 1.0 - q;
+        double a2 = a * a;
+        double a4 = a2 * a2;
+        double a7 = a4 * a2 * a;
+        double p = 1.0 + q * (7.0 + q * 16.0);
+        return 22.0 * (q * q) * a7 * p;
+    }
+    return 0.0;
+}
+
 /* -q w'(q), the term whose sum gives dN_w/dh. */
 double oracle_mqdw(double q)
 {
@@ -99,6 +129,7 @@ typedef struct {
     double box[3];    /* periodic box lengths */
     double origin[3]; /* non-periodic: bounding-box minimum */
     double ext[3];    /* periodic: box; non-periodic: one cubic extent for all three */
+    int kernel;       /* 0: M4 cubic spline, 1: Wendland C6 */
 } pset;
 
 typedef struct {
@@ -230,10 +261,10 @@ static inline void pair(const pset *ps, int64_t i, int64_t j, double h, double h
     if (r2 < h2) {
         double r = sqrt(r2);
         double q = r / h;
-        double w = oracle_w(q);
+        double w = ps->kernel ? oracle_w_c6(q) : oracle_w(q);
         a->sum_mw += ps->m[j] * w;
         a->sum_w += w;
-        a->sum_dw += oracle_mqdw(q);
+        a->sum_dw += ps->kernel ? oracle_mqdw_c6(q) : oracle_mqdw(q);
         a->count++;
     }
 }
@@ -291,12 +322,20 @@ static void eval_grid(const pset *ps, const bucket_grid *bg, int64_t i, double h
     }
 }
 
-static void finish(double h, const acc_t *a, double *rho, double *nw, double *dnw)
+/* rho = sigma h^-3 sum m w; N_w = (4 pi / 3) sigma sum w; dN_w/dh = (4 pi / 3) sigma h^-1 sum -q w'
+ * with sigma = 8/pi (M4) or 1365/(64 pi) (Wendland C6), i.e. (4 pi / 3) sigma = 32/3 or 1365/48. */
+static void finish(int kernel, double h, const acc_t *a, double *rho, double *nw, double *dnw)
 {
     const double pi = 3.14159265358979323846;
-    *rho = a->sum_mw * (8.0 / (pi * h * h * h));
-    *nw = (32.0 / 3.0) * a->sum_w;
-    *dnw = (32.0 / 3.0) * a->sum_dw / h;
+    if (kernel) {
+        *rho = a->sum_mw * (1365.0 / (64.0 * pi * h * h * h));
+        *nw = (1365.0 / 48.0) * a->sum_w;
+        *dnw = (1365.0 / 48.0) * a->sum_dw / h;
+    } else {
+        *rho = a->sum_mw * (8.0 / (pi * h * h * h));
+        *nw = (32.0 / 3.0) * a->sum_w;
+        *dnw = (32.0 / 3.0) * a->sum_dw / h;
+    }
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -304,9 +343,10 @@ static void finish(double h, const acc_t *a, double *rho, double *nw, double *dn
 /* ------------------------------------------------------------------------------------ */
 
 static void setup_pset(pset *ps, int64_t n, const double *x, const double *y, const double *z,
-                       const double *m, const double *box, int periodic)
+                       const double *m, const double *box, int periodic, int kernel)
 {
     memset(ps, 0, sizeof(*ps));
+    ps->kernel = kernel;
     ps->n = n;
     ps->x = x;
     ps->y = y;
@@ -349,10 +389,10 @@ static void setup_pset(pset *ps, int64_t n, const double *x, const double *y, co
 int oracle_eval(int64_t n, const double *x, const double *y, const double *z, const double *m,
                 const double *box, int periodic, int64_t n_targets, const int64_t *targets,
                 const double *h, int mode, double near_rel, double *rho, double *nw, double *dnw,
-                int64_t *count, int64_t *near_out)
+                int64_t *count, int64_t *near_out, int kernel)
 {
     pset ps;
-    setup_pset(&ps, n, x, y, z, m, box, periodic);
+    setup_pset(&ps, n, x, y, z, m, box, periodic, kernel);
     if (n_targets < 0) n_targets = n;
     bucket_grid grids[ORACLE_MAX_LEVEL + 1];
     memset(grids, 0, sizeof(grids));
@@ -368,7 +408,7 @@ int oracle_eval(int64_t n, const double *x, const double *y, const double *z, co
         acc_t a;
         if (mode == 0) eval_grid(&ps, &grids[level_for(&ps, h[t])], i, h[t], near_rel, &a);
         else eval_brute(&ps, i, h[t], near_rel, &a);
-        finish(h[t], &a, &rho[t], &nw[t], &dnw[t]);
+        finish(ps.kernel, h[t], &a, &rho[t], &nw[t], &dnw[t]);
         count[t] = a.count;
         if (near_out) near_out[t] = a.near;
     }
@@ -440,7 +480,7 @@ static int solve_set(const pset *ps, int64_t n_targets, const int64_t *targets, 
             if (mode == 0) eval_grid(ps, &grids[level_for(ps, hc)], i, hc, 0.0, &a);
             else eval_brute(ps, i, hc, 0.0, &a);
             double rho, nw, dnw;
-            finish(hc, &a, &rho, &nw, &dnw);
+            finish(ps->kernel, hc, &a, &rho, &nw, &dnw);
             pairs += a.count;
             h_inout[t] = hc; /* outputs always describe the last evaluation */
             rho_out[t] = rho;
@@ -499,10 +539,11 @@ static int solve_set(const pset *ps, int64_t n_targets, const int64_t *targets, 
 int oracle_solve(int64_t n, const double *x, const double *y, const double *z, const double *m,
                  const double *box, int periodic, double nngb, double tol, int max_iter,
                  int64_t n_targets, const int64_t *targets, int mode, double *h_inout,
-                 double *rho, double *nw, int64_t *count, int32_t *status, oracle_stats *st)
+                 double *rho, double *nw, int64_t *count, int32_t *status, oracle_stats *st,
+                 int kernel)
 {
     pset ps;
-    setup_pset(&ps, n, x, y, z, m, box, periodic);
+    setup_pset(&ps, n, x, y, z, m, box, periodic, kernel);
     if (n_targets < 0) n_targets = n;
     memset(st, 0, sizeof(*st));
     return solve_set(&ps, n_targets, targets, nngb, tol, max_iter, mode, h_inout, rho, nw, count,
@@ -514,7 +555,7 @@ int oracle_solve(int64_t n, const double *x, const double *y, const double *z, c
 int oracle_batch_solve(int64_t n_groups, const int64_t *offsets, const double *x, const double *y,
                        const double *z, const double *m, const double *nngb, const double *tol,
                        int max_iter, int mode, double *h_inout, double *rho, double *nw,
-                       int64_t *count, int32_t *status, oracle_stats *st)
+                       int64_t *count, int32_t *status, oracle_stats *st, int kernel)
 {
     memset(st, 0, sizeof(*st));
     const double nobox[3] = {0.0, 0.0, 0.0};
@@ -522,7 +563,7 @@ int oracle_batch_solve(int64_t n_groups, const int64_t *offsets, const double *x
         int64_t s = offsets[g], e = offsets[g + 1];
         if (e <= s) continue;
         pset ps;
-        setup_pset(&ps, e - s, x + s, y + s, z + s, m + s, nobox, 0);
+        setup_pset(&ps, e - s, x + s, y + s, z + s, m + s, nobox, 0, kernel);
         oracle_stats gs;
         memset(&gs, 0, sizeof(gs));
         int rc = solve_set(&ps, e - s, NULL, nngb[g], tol[g], max_iter, mode, h_inout + s, rho + s,

@@ -108,9 +108,9 @@ sph_status cuda_fail(sph_ctx *c, cudaError_t e, const char *where)
 sph_status check_params(sph_ctx *c, const sph_params *p)
 {
     if (!p) return fail(c, SPH_ERR_INVALID_ARG, "params is NULL");
-    if (p->kernel == SPH_KERNEL_WENDLAND_C6)
-        return fail(c, SPH_ERR_UNSUPPORTED, "the Wendland C6 kernel is not implemented");
-    if (p->kernel != SPH_KERNEL_M4) return fail(c, SPH_ERR_INVALID_ARG, "unknown kernel %d", p->kernel);
+    if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_WENDLAND_C6)
+        return fail(c, SPH_ERR_INVALID_ARG, "unknown kernel %d", p->kernel);
+    const double self = p->kernel == SPH_KERNEL_M4 ? 32.0 / 3.0 : 1365.0 / 48.0;
     if (p->precision != SPH_PREC_FP64 && p->precision != SPH_PREC_FP32_KAHAN)
         return fail(c, SPH_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->periodic != 0 && p->periodic != 1) return fail(c, SPH_ERR_INVALID_ARG, "periodic must be 0 or 1");
@@ -118,8 +118,8 @@ sph_status check_params(sph_ctx *c, const sph_params *p)
         for (int d = 0; d < 3; d++)
             if (!(p->box[d] > 0.0 && p->box[d] <= DBL_MAX))
                 return fail(c, SPH_ERR_INVALID_ARG, "box[%d] must be finite and > 0", d);
-    if (!(p->nngb > 32.0 / 3.0 && p->nngb <= 1e9))
-        return fail(c, SPH_ERR_INVALID_ARG, "nngb must exceed the self term 32/3 (got %g)", p->nngb);
+    if (!(p->nngb > self && p->nngb <= 1e9))
+        return fail(c, SPH_ERR_INVALID_ARG, "nngb must exceed the self term %g (got %g)", self, p->nngb);
     if (!(p->tol >= 0.0 && p->tol <= DBL_MAX)) return fail(c, SPH_ERR_INVALID_ARG, "tol must be >= 0");
     if (p->max_iter < 1 || p->max_iter > SPH_MAX_PASSES)
         return fail(c, SPH_ERR_INVALID_ARG, "max_iter must be in [1, %d]", SPH_MAX_PASSES);
@@ -194,6 +194,7 @@ SortArgs sort_args(sph_ctx *c)
     a.kl = c->kl;
     a.grid_cap = c->grid_cap;
     a.table_extra = c->tuning.table_extra;
+    a.self_floor = c->params.kernel == SPH_KERNEL_WENDLAND_C6 ? 1365.0 / 48.0 : 32.0 / 3.0;
     a.launches = &c->launches;
     return a;
 }
@@ -229,6 +230,7 @@ SolveArgs solve_args(sph_ctx *c)
     a.ds = c->ds;
     a.grid_cap = c->grid_cap;
     a.precision = c->params.precision;
+    a.kernel = c->params.kernel;
     a.density_grid = c->density_grid[c->params.precision == SPH_PREC_FP64 ? 0
                                       : c->tuning.direct_pct == 0           ? 2
                                                                             : 1];

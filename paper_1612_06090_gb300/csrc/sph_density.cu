@@ -227,12 +227,33 @@ __device__ __forceinline__ void m4_half(float q, float &w_half, float &dw_sixth)
     dw_sixth = q * (u2 - v2);
 }
 
+// The Wendland C6 shape with u = max(1-q, 0):
+//   w = u^8 (1 + 8q + 25q^2 + 32q^3),   -q w' = 22 q^2 u^7 (1 + 7q + 16q^2);
+// the sums carry w and -q w'/22.
+__device__ __forceinline__ void c6_shape(float q, float &w, float &dw_22)
+{
+    const float u = fmaxf(1.f - q, 0.f);
+    const float u2 = u * u, u4 = u2 * u2;
+    const float u7 = u4 * u2 * u, u8 = u4 * u4;
+    w = u8 * fmaf(q, fmaf(q, fmaf(q, 32.f, 25.f), 8.f), 1.f);
+    dw_22 = (q * q) * u7 * fmaf(q, fmaf(q, 16.f, 7.f), 1.f);
+}
+
+// kKern: 0 = M4 cubic spline, 1 = Wendland C6
+template <int kKern>
+__device__ __forceinline__ void shape32(float q, float &w, float &dw)
+{
+    if (kKern == 0) m4_half(q, w, dw);
+    else c6_shape(q, w, dw);
+}
+
 // One in-h pair in FP32 from its squared distance and the neighbour mass.
+template <int kKern>
 __device__ __forceinline__ void pair32(float2 e, float hinv2, Acc32 &A)
 {
     const float q = sqrt_approx(e.x * hinv2);
     float w, dw;
-    m4_half(q, w, dw);
+    shape32<kKern>(q, w, dw);
     A.p_mw = fmaf(e.y, w, A.p_mw);
     A.p_w += w;
     A.p_dw += dw;
@@ -271,11 +292,38 @@ __device__ __forceinline__ double mqdw64(double q)
     return 0.0;
 }
 
+__device__ __forceinline__ double w64_c6(double q)
+{
+    if (q < 1.0) {
+        const double a = __dsub_rn(1.0, q);
+        const double a2 = __dmul_rn(a, a);
+        const double a4 = __dmul_rn(a2, a2);
+        const double a8 = __dmul_rn(a4, a4);
+        const double p = __dadd_rn(1.0, __dmul_rn(q, __dadd_rn(8.0, __dmul_rn(q, __dadd_rn(25.0, __dmul_rn(q, 32.0))))));
+        return __dmul_rn(a8, p);
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double mqdw64_c6(double q)
+{
+    if (q < 1.0) {
+        const double a = __dsub_rn(1.0, q);
+        const double a2 = __dmul_rn(a, a);
+        const double a4 = __dmul_rn(a2, a2);
+        const double a7 = __dmul_rn(__dmul_rn(a4, a2), a);
+        const double p = __dadd_rn(1.0, __dmul_rn(q, __dadd_rn(7.0, __dmul_rn(q, 16.0))));
+        return __dmul_rn(__dmul_rn(__dmul_rn(22.0, __dmul_rn(q, q)), a7), p);
+    }
+    return 0.0;
+}
+
 struct Acc64 {
     double s_mw, s_w, s_dw;
     int count;
 };
 
+template <int kKern>
 __device__ __forceinline__ void pair64(const double4_32a &ti, const double4_32a &cj, double h,
                                        double h2, const SegInfo &S, Acc64 &A)
 {
@@ -290,10 +338,10 @@ __device__ __forceinline__ void pair64(const double4_32a &ti, const double4_32a 
     const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     if (r2 < h2) {
         const double q = __ddiv_rn(__dsqrt_rn(r2), h);
-        const double w = w64(q);
+        const double w = kKern == 0 ? w64(q) : w64_c6(q);
         A.s_mw = __dadd_rn(A.s_mw, __dmul_rn(cj.w, w));
         A.s_w = __dadd_rn(A.s_w, w);
-        A.s_dw = __dadd_rn(A.s_dw, mqdw64(q));
+        A.s_dw = __dadd_rn(A.s_dw, kKern == 0 ? mqdw64(q) : mqdw64_c6(q));
         A.count++;
     }
 }
@@ -314,7 +362,7 @@ struct LaneTarget {
 // in-h pairs fall across the targets.
 // kMode: 0 = FP64 (queue), 1 = FP32 with the queue until the in-h share is known, 2 = FP32
 // evaluated directly (no queue, no ring memory).
-template <int kMode>
+template <int kMode, int kKern>
 __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__restrict__ sidx,
                                       void *__restrict__ ring_raw, int cnt, int direct_pct,
                                       const LaneTarget &L,
@@ -334,9 +382,9 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
     auto drain_one = [&](int &head) {
         if (kF64) {
             const int j = ring64[head & (kRing - 1)][lane];
-            pair64(ti, pdbl[sidx[j]], h, h2, S, A64);
+            pair64<kKern>(ti, pdbl[sidx[j]], h, h2, S, A64);
         } else {
-            pair32(ring32[head & (kRing - 1)][lane], L.hinv2, A32);
+            pair32<kKern>(ring32[head & (kRing - 1)][lane], L.hinv2, A32);
         }
         head++;
     };
@@ -394,7 +442,7 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
                 if (r2 < L.h2) {
                     const float q = sqrt_approx(r2 * L.hinv2);
                     float w, dw;
-                    m4_half(q, w, dw);
+                    shape32<kKern>(q, w, dw);
                     A32.p_mw = fmaf(c.w, w, A32.p_mw);
                     A32.p_w += w;
                     A32.p_dw += dw;
@@ -413,7 +461,7 @@ __host__ __device__ constexpr int warp_smem_bytes()
     return kStageCap * 16 + (kMode == 0 ? kStageCap * 4 + kRing * 32 * 4 : kMode == 1 ? kRing * 32 * 8 : 0);
 }
 
-template <int kMode>
+template <int kMode, int kKern>
 __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
     k_density(SolveArgs a, const int32_t *__restrict__ todo)
 {
@@ -534,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
                     cnt += __popc(m);
                     if (cnt > kStage - 32) {
                         __syncwarp();
-                        flush<kMode>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+                        flush<kMode, kKern>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
                         staged += cnt;
                         cnt = 0;
                     }
@@ -543,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
         }
         __syncwarp();
         if (cnt > 0) {
-            flush<kMode>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+            flush<kMode, kKern>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
             staged += cnt;
         }
 
@@ -559,9 +607,15 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
             }
             if (active && L.s == 0) {
                 const double h = hd;
-                a.e_rho[p] = smw * (8.0 / (kPi * h * h * h));
-                a.e_nw[p] = (32.0 / 3.0) * sw;
-                a.e_dnw[p] = (32.0 / 3.0) * sdw / h;
+                if (kKern == 0) {
+                    a.e_rho[p] = smw * (8.0 / (kPi * h * h * h));
+                    a.e_nw[p] = (32.0 / 3.0) * sw;
+                    a.e_dnw[p] = (32.0 / 3.0) * sdw / h;
+                } else {
+                    a.e_rho[p] = smw * (1365.0 / (64.0 * kPi * h * h * h));
+                    a.e_nw[p] = (1365.0 / 48.0) * sw;
+                    a.e_dnw[p] = (1365.0 / 48.0) * sdw / h;
+                }
                 a.e_cnt[p] = count;
                 pairs += (unsigned long long)count;
             }
@@ -581,11 +635,15 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
             }
             if (active && L.s == 0) {
                 const float hi = 1.0f / hf;
-                // rho = (8/pi) h^-3 sum m w; N_w = (32/3) sum w; dN_w/dh = (32/3) h^-1 sum -q w'
-                // (the sums carry w/2 and -q w'/6)
-                a.e_rho32[p] = (2.0f * 2.546479089f) * (hi * hi * hi) * (smw - cmw);
-                a.e_nw32[p] = (2.0f * 10.66666667f) * (sw - cw);
-                a.e_dnw32[p] = (6.0f * 10.66666667f) * hi * (sdw - cdw);
+                // rho = sigma h^-3 sum m w; N_w = (4 pi/3) sigma sum w; dN_w/dh = (4 pi/3) sigma
+                // h^-1 sum -q w', with sigma = 8/pi (M4; the sums carry w/2 and -q w'/6) or
+                // 1365/(64 pi) (Wendland C6; the sums carry w and -q w'/22)
+                const float crho = kKern == 0 ? 2.0f * 2.546479089f : 6.788953041f;
+                const float cnw = kKern == 0 ? 2.0f * 10.66666667f : 28.4375f;
+                const float cdnw = kKern == 0 ? 6.0f * 10.66666667f : 22.0f * 28.4375f;
+                a.e_rho32[p] = crho * (hi * hi * hi) * (smw - cmw);
+                a.e_nw32[p] = cnw * (sw - cw);
+                a.e_dnw32[p] = cdnw * hi * (sdw - cdw);
                 a.e_cnt[p] = count;
                 pairs += (unsigned long long)count;
             }
@@ -604,13 +662,13 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
 
 }  // namespace
 
-template <int kMode>
+template <int kMode, int kKern>
 int blocks_per_sm()
 {
     const int bytes = kWarps * warp_smem_bytes<kMode>();
-    cudaFuncSetAttribute(k_density<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_density<kMode, kKern>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<kMode>, kThreads, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<kMode, kKern>, kThreads, bytes);
     return b > 0 ? b : 1;
 }
 
@@ -618,25 +676,29 @@ int mode_of(int precision, int direct_pct) { return precision == 0 ? 0 : direct_
 
 int density_blocks_per_sm(int precision, int direct_pct)
 {
+    // both kernels' attributes are set; the grid follows the M4 instantiation (the persistent
+    // grid is correct for any size, the work queue balances it)
     switch (mode_of(precision, direct_pct)) {
-    case 0: return blocks_per_sm<0>();
-    case 1: return blocks_per_sm<1>();
-    default: return blocks_per_sm<2>();
+    case 0: blocks_per_sm<0, 1>(); return blocks_per_sm<0, 0>();
+    case 1: blocks_per_sm<1, 1>(); return blocks_per_sm<1, 0>();
+    default: blocks_per_sm<2, 1>(); return blocks_per_sm<2, 0>();
     }
+}
+
+template <int kMode>
+void launch_mode(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
+{
+    const int bytes = kWarps * warp_smem_bytes<kMode>();
+    if (a.kernel == 0) k_density<kMode, 0><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
+    else k_density<kMode, 1><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
 }
 
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
     switch (mode_of(a.precision, a.direct_pct)) {
-    case 0:
-        k_density<0><<<a.density_grid, kThreads, kWarps * warp_smem_bytes<0>(), st>>>(a, todo);
-        break;
-    case 1:
-        k_density<1><<<a.density_grid, kThreads, kWarps * warp_smem_bytes<1>(), st>>>(a, todo);
-        break;
-    default:
-        k_density<2><<<a.density_grid, kThreads, kWarps * warp_smem_bytes<2>(), st>>>(a, todo);
-        break;
+    case 0: launch_mode<0>(a, todo, st); break;
+    case 1: launch_mode<1>(a, todo, st); break;
+    default: launch_mode<2>(a, todo, st); break;
     }
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();

@@ -20,6 +20,7 @@ struct SortArgs {
     KeyLayout kl;
     int grid_cap;          // upper bound on blocks per launch
     int table_extra;       // dense-table levels beyond one cell per particle (batch groups)
+    double self_floor;     // N_w of a lone particle (32/3 M4, 1365/48 Wendland C6)
     int *launches;         // host-side launch counter
 };
 
@@ -71,6 +72,7 @@ struct SolveArgs {
     int direct_pct;            // in-h percentage of the first tests above which the pair loop
                                // evaluates directly instead of queueing (101 = always queue)
     int precision;             // sph_precision
+    int kernel;                // sph_kernel: 0 M4 cubic spline, 1 Wendland C6
     int *launches;
     cudaEvent_t dens_ev[2];    // optional events recorded around the density launch
 };

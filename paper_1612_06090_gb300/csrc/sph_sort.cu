@@ -235,8 +235,8 @@ __global__ void k_cell_table(int64_t n, const uint64_t *__restrict__ key,
 __global__ void k_group_setup(int64_t n_groups, const int64_t *__restrict__ offsets,
                               const double *__restrict__ pos, int64_t n,
                               const double *__restrict__ nngb, const double *__restrict__ tol,
-                              KeyLayout kl, int table_extra, SegInfo *__restrict__ segs,
-                              int32_t *__restrict__ tsize, DevState *ds)
+                              KeyLayout kl, int table_extra, double self_floor,
+                              SegInfo *__restrict__ segs, int32_t *__restrict__ tsize, DevState *ds)
 {
     __shared__ double red[6][kSortThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -299,7 +299,7 @@ __global__ void k_group_setup(int64_t n_groups, const int64_t *__restrict__ offs
             si.pad = 0;
             segs[g] = si;
             tsize[g] = (int32_t)((1ll << (3 * lc)) + 1);
-            if (!(si.nngb > 32.0 / 3.0) || !(si.tol >= 0.0) || e < s) atomicOr(&ds->sort_status, kBadH);
+            if (!(si.nngb > self_floor) || !(si.tol >= 0.0) || e < s) atomicOr(&ds->sort_status, kBadH);
         }
         __syncthreads();
     }
@@ -338,7 +338,7 @@ cudaError_t launch_group_setup(const SortArgs &a, int64_t n_groups, const int64_
                                int32_t *tsize, int32_t *toff, cudaStream_t st)
 {
     k_group_setup<<<blocks_for(n_groups, 1, a.grid_cap), kSortThreads, 0, st>>>(
-        n_groups, offsets, pos, n, nngb, tol, a.kl, a.table_extra, a.segs, tsize, a.ds);
+        n_groups, offsets, pos, n, nngb, tol, a.kl, a.table_extra, a.self_floor, a.segs, tsize, a.ds);
     if (a.launches) *a.launches += 1;
     cudaError_t e = scan_exclusive(tsize, toff, n_groups, nullptr, nullptr, a.scan_aux, a.grid_cap, st,
                                    a.launches);

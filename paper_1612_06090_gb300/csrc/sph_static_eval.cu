@@ -215,6 +215,7 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     sa.kl = kl;
     sa.grid_cap = dev->num_sms * 16;
     sa.table_extra = 0;
+    sa.self_floor = 32.0 / 3.0;
     sa.launches = &launches;
     CUS(launch_keys_periodic(sa, n, pos_xyz_dev, mass_dev, sg, params->box, st));
     int which = 0;
@@ -251,6 +252,7 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     a.ds = c.ds;
     a.grid_cap = dev->num_sms * 16;
     a.precision = params->precision;
+    a.kernel = SPH_KERNEL_M4;
     a.density_grid = dev->density_grid[params->precision == SPH_PREC_FP64 ? 0 : 1];
     a.gmax = 32;
     a.group_shift = 1;

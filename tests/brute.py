@@ -27,8 +27,22 @@ def _mqdw(q):
     return np.where(q <= 0.5, inner, np.where(q < 1.0, outer, 0.0))
 
 
-def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, chunk=256):
+def _w_c6(q):
+    q = np.asarray(q, dtype=np.float64)
+    a = np.clip(1.0 - q, 0.0, None)
+    return a**8 * (1.0 + 8.0 * q + 25.0 * q * q + 32.0 * q**3)
+
+
+def _mqdw_c6(q):
+    q = np.asarray(q, dtype=np.float64)
+    a = np.clip(1.0 - q, 0.0, None)
+    return 22.0 * q * q * a**7 * (1.0 + 7.0 * q + 16.0 * q * q)
+
+
+def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, chunk=256, kernel="m4"):
     """rho, N_w, dN_w/dh, count for each target at its own h, by direct summation."""
+    wf, dwf = (_w, _mqdw) if kernel == "m4" else (_w_c6, _mqdw_c6)
+    sigma = 8.0 / math.pi if kernel == "m4" else 1365.0 / (64.0 * math.pi)
     pos = np.asarray(pos, dtype=np.float64)
     mass = np.asarray(mass, dtype=np.float64)
     n = pos.shape[1]
@@ -49,11 +63,11 @@ def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, chu
         inside = r2 < hh * hh
         r = np.sqrt(r2)
         q = np.where(inside, r / hh, 1.0)
-        w = np.where(inside, _w(q), 0.0)
-        dw = np.where(inside, _mqdw(q), 0.0)
+        w = np.where(inside, wf(q), 0.0)
+        dw = np.where(inside, dwf(q), 0.0)
         hv = hh[:, 0]
-        rho[s:s + chunk] = (w * mass[None, :]).sum(axis=1) * 8.0 / (math.pi * hv ** 3)
-        nw[s:s + chunk] = 32.0 / 3.0 * w.sum(axis=1)
-        dnw[s:s + chunk] = 32.0 / 3.0 * dw.sum(axis=1) / hv
+        rho[s:s + chunk] = (w * mass[None, :]).sum(axis=1) * sigma / hv ** 3
+        nw[s:s + chunk] = 4.0 * math.pi / 3.0 * sigma * w.sum(axis=1)
+        dnw[s:s + chunk] = 4.0 * math.pi / 3.0 * sigma * dw.sum(axis=1) / hv
         count[s:s + chunk] = inside.sum(axis=1)
     return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}

@@ -91,8 +91,11 @@ def test_create_rejects_bad_arguments_on_the_host(B):
         st, ctx = B.sph_create(B.make_params(**kw), 100)
         assert st == B.SPH_ERR_INVALID_ARG, kw
         assert ctx is None
-    st, ctx = B.sph_create(B.make_params(kernel=B.SPH_KERNEL_WENDLAND_C6), 100)
-    assert st == B.SPH_ERR_UNSUPPORTED
+    # Wendland C6's self term is 1365/48 = 28.4375: a target below it is rejected
+    st, ctx = B.sph_create(B.make_params(kernel=B.SPH_KERNEL_WENDLAND_C6, nngb=20.0), 100)
+    assert st == B.SPH_ERR_INVALID_ARG
+    st, ctx = B.sph_create(B.make_params(kernel=7), 100)
+    assert st == B.SPH_ERR_INVALID_ARG
     for cap in (0, -5, 1 << 31):
         st, ctx = B.sph_create(good, cap)
         assert st == B.SPH_ERR_INVALID_ARG

@@ -372,3 +372,49 @@ def test_autotune_picks_a_tuning_caches_it_and_keeps_results(tmp_path):
     assert s2.tuning() == best
     s2.close()
     assert open(cache).read().strip()
+
+
+# ---- the paper's Wendland C6 kernel at 295 neighbours ------------------------------------------
+
+C6 = B.SPH_KERNEL_WENDLAND_C6
+
+
+def _c6_solver(n, precision, **kw):
+    return B.Solver(n, precision=precision, kernel=C6, nngb=295.0, tol=5.0, **kw)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_wendland_c6_eval_against_oracle(precision):
+    wl = inputs.uniform_box(n=20000, seed=61, nngb=295.0)
+    rng = np.random.default_rng(9)
+    h = wl.h0 * rng.uniform(0.7, 1.3, size=wl.n)
+    s = _c6_solver(wl.n, precision)
+    s.sort(T(wl.pos), T(wl.mass))
+    g = {k: np_(v) for k, v in s.evaluate(T(h)).items()}
+    s.close()
+    if precision == FP64:
+        o = oracle.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6")
+        check_eval(g, o, rtol=1e-12, count_exact=True)
+    else:
+        o = oracle.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6", near_rel=2e-6)
+        check_eval(g, o, rtol=1e-5, count_exact=False, near=o["near"])
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_wendland_c6_solve_clusters_sampled(precision):
+    wl = inputs.plummer_clusters(n=1 << 18, seed=62, nngb=295.0, tol=5.0)
+    s = _c6_solver(wl.n, precision)
+    s.sort(T(wl.pos), T(wl.mass))
+    r = s.solve(T(wl.h0))
+    torch.cuda.synchronize()
+    g = {k: (np_(v) if torch.is_tensor(v) else v) for k, v in r.items()}
+    s.close()
+    assert g["status"] == B.SPH_OK
+    assert np.all(np.abs(g["nw"] - 295.0) <= 5.0 + 1e-3)
+    tg = np.sort(np.random.default_rng(63).choice(wl.n, size=400, replace=False))
+    o = oracle.solve(wl.pos, wl.mass, wl.h0[tg], nngb=295.0, tol=5.0, targets=tg, kernel="wendland_c6")
+    gs = {k: g[k][tg] for k in ("h", "rho", "count", "nw")}
+    fp64 = precision == FP64
+    check_solve(wl.pos, wl.mass, wl.box, True, 295.0, 5.0, gs, o, tg, rtol=1e-12 if fp64 else 1e-5,
+                delta=(1e-9 if fp64 else 1e-5) * 295.0, max_mismatch_frac=0.03, count_exact=fp64,
+                kernel="wendland_c6")

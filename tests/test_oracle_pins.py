@@ -351,3 +351,57 @@ def test_batch_group_brute_force_at_solution():
         b = brute.evaluate(wl.pos[:, s:e], wl.mass[s:e], r["h"][s:e], periodic=False)
         np.testing.assert_array_equal(b["count"], r["count"][s:e])
         np.testing.assert_allclose(b["rho"], r["rho"][s:e], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------------------
+# Wendland C6 (the paper's kernel, Sec. II-B)
+# --------------------------------------------------------------------------------------
+
+def test_wendland_c6_normalisation_and_shape():
+    # int W d^3r = 1365/(64 pi) * 4 pi * int q^2 w = (1365/16) int_0^1 q^2 w(q) dq = 1
+    val, _ = integrate.quad(lambda q: q * q * oracle.w_c6(q), 0.0, 1.0, epsabs=1e-15, epsrel=1e-14)
+    assert abs(1365.0 / 16.0 * val - 1.0) < 1e-12
+    assert oracle.w_c6(0.0) == 1.0
+    for q in (1.0, 1.2, 3.0):
+        assert oracle.w_c6(q) == 0.0 and oracle.mqdw_c6(q) == 0.0
+    # contact of order 8 at the support edge (C6 for the radial function): w(1-e)/e^8 -> w's
+    # polynomial factor at q = 1, which is 1 + 8 + 25 + 32 = 66
+    for e in (1e-2, 1e-3):
+        assert oracle.w_c6(1.0 - e) / e**8 == pytest.approx(66.0, rel=0.2 * e / 1e-2)
+    # even at the origin: no linear term
+    assert abs((oracle.w_c6(1e-6) - 1.0) / 1e-6) < 1e-4
+
+
+def test_wendland_c6_mqdw_is_minus_q_derivative():
+    for q in np.linspace(0.02, 0.98, 49):
+        d1, _ = _derivs(oracle.w_c6, q, 1e-6)
+        assert oracle.mqdw_c6(q) == pytest.approx(-q * d1, rel=1e-6, abs=1e-9)
+
+
+def test_wendland_c6_matches_brute_force_and_finite_difference():
+    wl = inputs.uniform_box(n=3000, seed=17, nngb=295.0)
+    rng = np.random.default_rng(2)
+    h = wl.h0 * rng.uniform(0.8, 1.2, size=wl.n)
+    o = oracle.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6")
+    b = brute.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6")
+    np.testing.assert_array_equal(o["count"], b["count"])
+    np.testing.assert_allclose(o["rho"], b["rho"], rtol=1e-13)
+    np.testing.assert_allclose(o["nw"], b["nw"], rtol=1e-13)
+    tg = np.arange(0, wl.n, 97)
+    eps = 1e-7
+    up = oracle.evaluate(wl.pos, wl.mass, h[tg] * (1 + eps), targets=tg, kernel="wendland_c6")
+    dn = oracle.evaluate(wl.pos, wl.mass, h[tg] * (1 - eps), targets=tg, kernel="wendland_c6")
+    fd = (up["nw"] - dn["nw"]) / (2 * eps * h[tg])
+    np.testing.assert_allclose(o["dnw"][tg], fd, rtol=2e-5)
+    # for a uniform Poisson field the neighbours other than the particle itself contribute
+    # n m int W = the mean density on average; the self term m W(0) comes on top
+    self_term = wl.mass * 1365.0 / (64.0 * math.pi * h**3)
+    assert abs(np.mean(o["rho"] - self_term) - 1.0) < 0.01
+    assert np.median(o["rho"]) > 1.05  # the self term is ~10 % at 295 neighbours
+
+
+def test_wendland_c6_solve_converges_in_band():
+    wl = inputs.uniform_box(n=4096, seed=18, nngb=295.0)
+    r = oracle.solve(wl.pos, wl.mass, wl.h0, nngb=295.0, tol=5.0, kernel="wendland_c6")
+    assert np.all(r["status"] == 0)
+    assert np.all(np.abs(r["nw"] - 295.0) <= 5.0)
