@@ -218,9 +218,11 @@ __device__ __forceinline__ void merge32(Acc32 &A)
 //   w = 2 u^3 - v^3,   -q w' = 6 q (u^2 - v^2),
 // both zero for q >= 1, with no branch on q.  The sums carry w/2 and -q w'/6; the factors
 // 2 and 6 are applied once per target.
+// kInside: the caller already knows q < 1 (up to one rounding), so u needs no clamp.
+template <bool kInside = false>
 __device__ __forceinline__ void m4_half(float q, float &w_half, float &dw_sixth)
 {
-    const float u = fmaxf(1.f - q, 0.f);
+    const float u = kInside ? 1.f - q : fmaxf(1.f - q, 0.f);
     const float v = fmaxf(fmaf(-2.f, q, 1.f), 0.f);
     const float u2 = u * u, v2 = v * v;
     w_half = fmaf(-0.5f * v, v2, u2 * u);
@@ -230,9 +232,10 @@ __device__ __forceinline__ void m4_half(float q, float &w_half, float &dw_sixth)
 // The Wendland C6 shape with u = max(1-q, 0):
 //   w = u^8 (1 + 8q + 25q^2 + 32q^3),   -q w' = 22 q^2 u^7 (1 + 7q + 16q^2);
 // the sums carry w and -q w'/22.
+template <bool kInside = false>
 __device__ __forceinline__ void c6_shape(float q, float &w, float &dw_22)
 {
-    const float u = fmaxf(1.f - q, 0.f);
+    const float u = kInside ? 1.f - q : fmaxf(1.f - q, 0.f);
     const float u2 = u * u, u4 = u2 * u2;
     const float u7 = u4 * u2 * u, u8 = u4 * u4;
     w = u8 * fmaf(q, fmaf(q, fmaf(q, 32.f, 25.f), 8.f), 1.f);
@@ -240,11 +243,11 @@ __device__ __forceinline__ void c6_shape(float q, float &w, float &dw_22)
 }
 
 // kKern: 0 = M4 cubic spline, 1 = Wendland C6
-template <int kKern>
+template <int kKern, bool kInside = false>
 __device__ __forceinline__ void shape32(float q, float &w, float &dw)
 {
-    if (kKern == 0) m4_half(q, w, dw);
-    else c6_shape(q, w, dw);
+    if (kKern == 0) m4_half<kInside>(q, w, dw);
+    else c6_shape<kInside>(q, w, dw);
 }
 
 // One in-h pair in FP32 from its squared distance and the neighbour mass.
@@ -442,7 +445,7 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
                 if (r2 < L.h2) {
                     const float q = sqrt_approx(r2 * L.hinv2);
                     float w, dw;
-                    shape32<kKern>(q, w, dw);
+                    shape32<kKern, true>(q, w, dw);
                     A32.p_mw = fmaf(c.w, w, A32.p_mw);
                     A32.p_w += w;
                     A32.p_dw += dw;

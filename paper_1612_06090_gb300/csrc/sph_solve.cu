@@ -105,12 +105,17 @@ __global__ void k_set_loop(cudaGraphConditionalHandle handle, const DevState *ds
     cudaGraphSetConditional(handle, ds->loop_flag ? 1u : 0u);
 }
 
-// Work-item heads: a new item starts at every multiple of gmax, whenever the grouping
-// bucket (level + octree cell at that level, segment included) changes, and around
-// single-target ("big") entries.
+// Work-item heads: a new item starts at every multiple of gmax and around single-target
+// ("big") entries.  While the todo list is dense (at least 1/8 of the particles) consecutive
+// targets stay together if they share an octree cell at the coarser of their two grouping
+// levels and those levels differ by at most one; once it is sparse they must have the same
+// level and share the cell at it (long runs of far-apart targets would otherwise stretch an
+// item's query box).  The segment is part of every key, so items never cross segments.
+// The item's query box uses the targets' actual bounds, so the rule only steers efficiency.
 __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
 {
     const int T = a.ds->pass_count;
+    const bool dense = 8 * (int64_t)T >= a.n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int p = todo[t];
         const uint64_t k = a.key[p];
@@ -126,7 +131,13 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
             uint64_t prep;
             bool bigp;
             bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp);
-            head = bigp || lp != l || prep != pre;
+            if (dense) {
+                const int m = lp < l ? lp : l;
+                head = bigp || (l - lp > 1) || (lp - l > 1) ||
+                       (k >> (3 * (a.kl.lmax - m))) != (kp >> (3 * (a.kl.lmax - m)));
+            } else {
+                head = bigp || lp != l || prep != pre;
+            }
         }
         a.flags[t] = head;
     }
