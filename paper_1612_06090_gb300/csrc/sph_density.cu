@@ -356,7 +356,50 @@ struct LaneTarget {
     float h2;          // h^2 for the test (FP64 path: widened radius); -1 for idle lanes
     float hinv2;
     int slices, s;
+    int sh;            // log2(slices)
 };
+
+// Stage layout of the packed FP32 path (kMode 2).  Candidate slot j is tested by slice
+// s = j mod S at step k = j / S (S = slices).  Steps 2i and 2i + 1 of one slice share two
+// float4s, (x0, x1, y0, y1) and (z0, z1, m0, m1), so a lane loads two candidates as packed
+// coordinate pairs and evaluates both with two-wide FP32 instructions.
+__device__ __forceinline__ void stage_pair_put(float *__restrict__ st, int j, int sh, float x,
+                                               float y, float z, float m)
+{
+    const int k = j >> sh, s = j & ((1 << sh) - 1);
+    float *f = st + ((((k >> 1) << sh) + s) << 3) + (k & 1);
+    f[0] = x;
+    f[2] = y;
+    f[4] = z;
+    f[6] = m;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Two candidates at once, the same roundings as the scalar shape functions: q is clamped
+// to at most 1 (q comes from the unclamped r^2 / h^2 of either candidate, padding
+// included), so a candidate outside h contributes exactly zero when its partner is inside.
+template <int kKern>
+__device__ __forceinline__ void shape32x2(float2 q, float2 &w, float2 &dw)
+{
+    const float2 one = f2(1.f, 1.f), m1 = f2(-1.f, -1.f);
+    const float2 u = __ffma2_rn(q, m1, one);  // 1 - q >= 0
+    if (kKern == 0) {
+        float2 v = __ffma2_rn(q, f2(-2.f, -2.f), one);
+        v = f2(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f));
+        const float2 u2 = __fmul2_rn(u, u), v2 = __fmul2_rn(v, v);
+        w = __ffma2_rn(__fmul2_rn(f2(-0.5f, -0.5f), v), v2, __fmul2_rn(u2, u));
+        dw = __fmul2_rn(q, __ffma2_rn(v2, m1, u2));
+    } else {
+        const float2 u2 = __fmul2_rn(u, u), u4 = __fmul2_rn(u2, u2);
+        const float2 u7 = __fmul2_rn(__fmul2_rn(u4, u2), u), u8 = __fmul2_rn(u4, u4);
+        const float2 p3 =
+            __ffma2_rn(q, __ffma2_rn(q, __ffma2_rn(q, f2(32.f, 32.f), f2(25.f, 25.f)), f2(8.f, 8.f)), one);
+        const float2 p2 = __ffma2_rn(q, __ffma2_rn(q, f2(16.f, 16.f), f2(7.f, 7.f)), one);
+        w = __fmul2_rn(u8, p3);
+        dw = __fmul2_rn(__fmul2_rn(__fmul2_rn(q, q), u7), p2);
+    }
+}
 
 // Test all staged candidates, queue the in-h ones per lane (ring of kRing entries), and
 // evaluate them in warp-wide rounds.  Only rounds in which every lane has a queued pair run
@@ -376,6 +419,51 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
     constexpr bool kF64 = kMode == 0;
     constexpr bool kQueue = kMode != 2;
     const int lane = lane_id();
+    if (kMode == 2) {
+        // pad to a multiple of 2 S (an even number of steps per slice) with candidates that
+        // are never within h
+        const int pad = (cnt + (2 << L.sh) - 1) & ~((2 << L.sh) - 1);
+        for (int j = cnt + lane; j < pad; j += 32)
+            stage_pair_put((float *)stage, j, L.sh, 3e18f, 3e18f, 3e18f, 0.f);
+        __syncwarp();
+        const int npair = pad >> (L.sh + 1);
+        const float2 ntx = f2(-L.tx, -L.tx), nty = f2(-L.ty, -L.ty), ntz = f2(-L.tz, -L.tz);
+        const float2 hinv2 = f2(L.hinv2, L.hinv2);
+        const float4 *__restrict__ st4 = stage + 2 * L.s;
+        for (int ib = 0; ib < npair; ib += 32) {
+            const int ie = ib + 32 < npair ? ib + 32 : npair;
+            float2 pmw = f2(0.f, 0.f), pw = pmw, pdw = pmw, pc = pmw;
+#pragma unroll 4
+            for (int i = ib; i < ie; i++) {
+                const float4 A = st4[2 * (i << L.sh)], B = st4[2 * (i << L.sh) + 1];
+                const float2 dx = __fadd2_rn(f2(A.x, A.y), ntx);
+                const float2 dy = __fadd2_rn(f2(A.z, A.w), nty);
+                const float2 dz = __fadd2_rn(f2(B.x, B.y), ntz);
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const bool in0 = r2.x < L.h2, in1 = r2.y < L.h2;
+                // the pair body runs when either candidate is within h; a step in which no
+                // lane has one costs only the test
+                if (in0 || in1) {
+                    pc = __fadd2_rn(pc, f2(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f));
+                    const float2 x = __fmul2_rn(r2, hinv2);
+                    const float2 q = f2(fminf(sqrt_approx(x.x), 1.f), fminf(sqrt_approx(x.y), 1.f));
+                    float2 w, dw;
+                    shape32x2<kKern>(q, w, dw);
+                    pmw = __ffma2_rn(f2(B.z, B.w), w, pmw);
+                    pw = __fadd2_rn(pw, w);
+                    pdw = __fadd2_rn(pdw, dw);
+                }
+            }
+            // at most 32 terms per partial sum, as in the scalar paths
+            A32.p_mw = pmw.x + pmw.y;
+            A32.p_w = pw.x + pw.y;
+            A32.p_dw = pdw.x + pdw.y;
+            A32.count += (int)(pc.x + pc.y);
+            merge32(A32);
+        }
+        __syncwarp();
+        return;
+    }
     // pad to a multiple of 32 with candidates that are never within h
     const int pad = (cnt + 31) & ~31;
     for (int j = cnt + lane; j < pad; j += 32) stage[j] = make_float4(3e18f, 3e18f, 3e18f, 0.f);
@@ -458,10 +546,18 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
     __syncwarp();
 }
 
+// Per-warp shared memory: the stage, the mode's queue memory, then the item's cell table
+// (exclusive prefix of the cell sizes and first particle of every cell).
+template <int kMode>
+__host__ __device__ constexpr int warp_cell_offset()
+{
+    return kStageCap * 16 + (kMode == 0 ? kStageCap * 4 + kRing * 32 * 4 : kMode == 1 ? kRing * 32 * 8 : 0);
+}
+
 template <int kMode>
 __host__ __device__ constexpr int warp_smem_bytes()
 {
-    return kStageCap * 16 + (kMode == 0 ? kStageCap * 4 + kRing * 32 * 4 : kMode == 1 ? kRing * 32 * 8 : 0);
+    return warp_cell_offset<kMode>() + 2 * kMaxCells * 4;
 }
 
 template <int kMode, int kKern>
@@ -475,6 +571,8 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
     float4 *stage = (float4 *)wbase;
     int *sidx = (int *)(wbase + kStageCap * 16);
     void *ring = wbase + kStageCap * 16 + (kF64 ? kStageCap * 4 : 0);
+    int *cpre = (int *)(wbase + warp_cell_offset<kMode>());
+    int *cbeg = cpre + kMaxCells;
     const int n_items = a.ds->n_items;
     const int todo_count = a.ds->pass_count;
     const int pass = a.ds->pass;
@@ -492,6 +590,7 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
         while (Gp < G) Gp <<= 1;
         LaneTarget L;
         L.slices = 32 / Gp;
+        L.sh = 5 - (31 - __clz(Gp));
         const int t = lane & (Gp - 1);
         L.s = lane / Gp;
         const bool active = t < G;
@@ -553,42 +652,74 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
         Acc64 A64 = {0.0, 0.0, 0.0, 0};
         int cnt = 0;
         int staged = 0;
-        for (int c = 0; c < ncell; c++) {
-            const long long rc = __shfl_sync(kFull, (c < 32) ? rr[0] : rr[1], c & 31);
-            const int rbeg = (int)(rc & 0xffffffffll), rend = (int)(rc >> 32);
-            for (int base = rbeg; base < rend; base += 64) {
-                // two independent 16-byte loads per lane before either is used
-                const int j0 = base + lane, j1 = base + 32 + lane;
-                uint4 P0 = make_uint4(0, 0, 0, 0), P1 = make_uint4(0, 0, 0, 0);
-                if (j0 < rend) P0 = a.pfix[j0];
-                if (j1 < rend) P1 = a.pfix[j1];
+        int total = 0;
+        // The item's cells (lane holds cells lane and lane + 32) are streamed as one list in
+        // cell order: an exclusive prefix of the cell sizes maps position f of the list to
+        // particle cbeg[c] + f - cpre[c] of the last cell c with cpre[c] <= f.  Cells past
+        // ncell are empty, so every position maps into a real cell.  Each lane's positions
+        // only grow, so it keeps its current cell (index offset, start of the next cell) in
+        // registers and searches the table only when it passes into another cell.
+        {
+            const int b0 = (int)(rr[0] & 0xffffffffll), n0 = (int)(rr[0] >> 32) - b0;
+            const int b1 = (int)(rr[1] & 0xffffffffll), n1 = (int)(rr[1] >> 32) - b1;
+            const int i0 = warp_inclusive_scan(n0), i1 = warp_inclusive_scan(n1);
+            const int tot0 = __shfl_sync(kFull, i0, 31);
+            total = tot0 + __shfl_sync(kFull, i1, 31);
+            __syncwarp();  // the previous item's reads of the table are done
+            cpre[lane] = i0 - n0;
+            cbeg[lane] = b0;
+            cpre[lane + 32] = tot0 + i1 - n1;
+            cbeg[lane + 32] = b1;
+            __syncwarp();
+        }
+        int cc = 0, coff = cbeg[0], cnxt = cpre[1];
+        for (int base = 0; base < total; base += 64) {
+            // two independent 16-byte loads per lane before either is used
+            int jj[2];
+            uint4 PP[2];
 #pragma unroll
-                for (int half = 0; half < 2; half++) {
-                    const int j = half ? j1 : j0;
-                    const uint4 &Pj = half ? P1 : P0;
-                    int rj[3] = {0, 0, 0};
-                    bool in = j < rend && in_query(G3, Pj, rj);
-                    float fx = 0.f, fy = 0.f, fz = 0.f;
-                    if (in) {
-                        fx = (float)rj[0] * qf[0];
-                        fy = (float)rj[1] * qf[1];
-                        fz = (float)rj[2] * qf[2];
-                        const float ex = fx - ccx, ey = fy - ccy, ez = fz - ccz;
-                        in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= ball2;
-                    }
-                    const unsigned m = __ballot_sync(kFull, in);
-                    if (in) {
-                        const int slot = cnt + __popc(m & lanemask_lt());
-                        stage[slot] = make_float4(fx, fy, fz, __uint_as_float(Pj.w));
-                        if (kF64) sidx[slot] = j;
-                    }
-                    cnt += __popc(m);
-                    if (cnt > kStage - 32) {
-                        __syncwarp();
-                        flush<kMode, kKern>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
-                        staged += cnt;
-                        cnt = 0;
-                    }
+            for (int half = 0; half < 2; half++) {
+                const int f = base + 32 * half + lane;
+                if (f < total && cnxt <= f) {
+                    int c = cc;
+#pragma unroll
+                    for (int step = kMaxCells / 2; step > 0; step >>= 1)
+                        if (c + step < kMaxCells && cpre[c + step] <= f) c += step;
+                    cc = c;
+                    coff = cbeg[c] - cpre[c];
+                    cnxt = c + 1 < kMaxCells ? cpre[c + 1] : INT_MAX;
+                }
+                jj[half] = f < total ? f + coff : -1;
+                PP[half] = make_uint4(0, 0, 0, 0);
+                if (jj[half] >= 0) PP[half] = a.pfix[jj[half]];
+            }
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int j = jj[half];
+                const uint4 &Pj = PP[half];
+                int rj[3] = {0, 0, 0};
+                bool in = j >= 0 && in_query(G3, Pj, rj);
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                if (in) {
+                    fx = (float)rj[0] * qf[0];
+                    fy = (float)rj[1] * qf[1];
+                    fz = (float)rj[2] * qf[2];
+                    const float ex = fx - ccx, ey = fy - ccy, ez = fz - ccz;
+                    in = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= ball2;
+                }
+                const unsigned m = __ballot_sync(kFull, in);
+                if (in) {
+                    const int slot = cnt + __popc(m & lanemask_lt());
+                    if (kMode == 2) stage_pair_put((float *)stage, slot, L.sh, fx, fy, fz, __uint_as_float(Pj.w));
+                    else stage[slot] = make_float4(fx, fy, fz, __uint_as_float(Pj.w));
+                    if (kF64) sidx[slot] = j;
+                }
+                cnt += __popc(m);
+                if (cnt > kStage - 32) {
+                    __syncwarp();
+                    flush<kMode, kKern>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+                    staged += cnt;
+                    cnt = 0;
                 }
             }
         }
