@@ -100,6 +100,7 @@ struct ItemGeom {
     int level;        // enumeration level
     uint32_t c_lo[3]; // first cell per dimension
     int nc[3];        // cells per dimension
+    int64_t cstart[3];  // start of the first cell relative to X0 (fixed point; non-full dims)
 };
 
 // All item geometry is bounds for culling, so it is computed in FP32 with margins that
@@ -147,11 +148,13 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
         if (G.full[d]) {
             G.c_lo[d] = 0;
             G.nc[d] = 1 << l;
+            G.cstart[d] = 0;
         } else if (S.periodic) {
             const uint32_t alo = G.X0[d] + (uint32_t)G.lo[d];
             const uint32_t ahi = G.X0[d] + (uint32_t)G.hi[d];
             G.c_lo[d] = alo >> s;
             G.nc[d] = (int)((((ahi >> s) - (alo >> s)) & cmask) + 1);
+            G.cstart[d] = G.lo[d] - (int64_t)(alo & ((1u << s) - 1u));
         } else {
             int64_t alo = (int64_t)G.X0[d] + G.lo[d];
             int64_t ahi = (int64_t)G.X0[d] + G.hi[d];
@@ -159,18 +162,31 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
             if (ahi > 2147483647ll) ahi = 2147483647ll;
             G.c_lo[d] = (uint32_t)(alo >> s);
             G.nc[d] = ahi >= alo ? (int)((ahi >> s) - (alo >> s) + 1) : 0;
+            G.cstart[d] = ((alo >> s) << s) - (int64_t)G.X0[d];
         }
     }
 }
 
-// Ranges of the item's cells; lane holds cells `lane` and `lane + 32`.
+// Ranges of the item's cells; lane holds cells `lane` and `lane + 32`.  A cell that lies
+// entirely outside the staging ball (centre cc, squared radius ball2, both in the FP32 offset
+// units of the item) can hold no candidate, so its range is left empty: no lookup, no loads.
+// The test only drops cells whose nearest point is farther than the ball radius by a
+// relative 1e-4, far above the rounding of the FP32 cell bounds (a few 1e-7 of the extent).
 __device__ __forceinline__ void item_ranges(const ItemGeom &G, int g, const SegInfo &S,
                                             const KeyLayout &kl, const int32_t *__restrict__ ctab,
                                             const uint64_t *__restrict__ key, int ncell,
+                                            const float cc[3], float ball2, const float qf[3],
                                             long long r[2])
 {
     const int lane = lane_id();
     const uint32_t cmask = (uint32_t)((1ull << G.level) - 1);
+    // first cell's start and the cell size per dimension in FP32 offset units (warp-uniform)
+    float c0f[3], csf[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        csf[d] = (float)(1ll << (kl.coord_bits - G.level)) * qf[d];
+        c0f[d] = (float)G.cstart[d] * qf[d];
+    }
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const int c = lane + 32 * k;
@@ -179,6 +195,16 @@ __device__ __forceinline__ void item_ranges(const ItemGeom &G, int g, const SegI
             const int ix = c % G.nc[0];
             const int iy = (c / G.nc[0]) % G.nc[1];
             const int iz = c / (G.nc[0] * G.nc[1]);
+            const int id[3] = {ix, iy, iz};
+            float dist2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (G.full[d]) continue;
+                const float flo = fmaf((float)id[d], csf[d], c0f[d]), fhi = flo + csf[d];
+                const float dd = fmaxf(fmaxf(flo - cc[d], cc[d] - fhi), 0.f);
+                dist2 = fmaf(dd, dd, dist2);
+            }
+            if (dist2 > ball2 * 1.0001f) continue;
             const uint32_t cx = (G.c_lo[0] + ix) & cmask;
             const uint32_t cy = (G.c_lo[1] + iy) & cmask;
             const uint32_t cz = (G.c_lo[2] + iz) & cmask;
@@ -626,9 +652,6 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
             if (lane == 0) atomicOr(&a.ds->status, 8);
             continue;
         }
-        long long rr[2];
-        item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, rr);
-
         // A candidate can lie within h of some target only inside the ball around the
         // centre of the targets' box of radius (half-diagonal + h_max); staging keeps the
         // box test (exact, integer) and adds this ball test (FP32 with a margin that covers
@@ -646,6 +669,12 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
             ccz = 0.5f * ((float)G3.bmin[2] + (float)G3.bmax[2]) * qf[2];
             const float Rm = (sqrtf(half2) + G3.hmax) * (1.0f + 1e-5f) + 8.0f * qm;
             ball2 = Rm * Rm;
+        }
+
+        long long rr[2];
+        {
+            const float cc[3] = {ccx, ccy, ccz};
+            item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, cc, ball2, qf, rr);
         }
 
         Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
