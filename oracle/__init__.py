@@ -13,6 +13,8 @@ w_c6(q), mqdw_c6(q)          Wendland C6 shape (Sec. II-B kernel) and -q w'(q)
 evaluate(...)                one fixed-h density evaluation      (Eq. 1, Listing 1)
 solve(...)                   the h iteration on one particle set (Sec. IV-A, Listing 3)
 batch_solve(...)             the same over independent non-periodic groups
+knn(...)                     h = distance to the K-th nearest particle, rho at that h
+                             (Sec. IV-C, the selection of the K nearest)
 """
 from __future__ import annotations
 
@@ -94,6 +96,9 @@ def _load():
     lib.oracle_batch_solve.argtypes = [ctypes.c_int64, ip, dp, dp, dp, dp, dp, dp, ctypes.c_int,
                                        ctypes.c_int, dp, dp, dp, ip, i32p,
                                        ctypes.POINTER(OracleStats), ctypes.c_int]
+    lib.oracle_knn.restype = ctypes.c_int
+    lib.oracle_knn.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int64, ip, ctypes.c_int, dp, dp, dp, ip, i32p, ctypes.c_int]
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     _lib = lib
@@ -232,3 +237,33 @@ def batch_solve(offsets, pos, mass, h0, nngb, tol, max_iter=64, mode="grid", ker
     if rc != 0:
         raise MemoryError("oracle_batch_solve failed to allocate")
     return {"h": h, "rho": rho, "nw": nw, "count": count, "status": status, "stats": st.to_dict()}
+
+
+def knn(pos, mass, k, box=(1.0, 1.0, 1.0), periodic=True, targets=None, mode="grid", kernel="m4"):
+    """k-nearest-neighbour smoothing lengths for the targets (None: all particles).
+
+    h = distance to the k-th nearest particle (the particle itself is the first, at r = 0),
+    every squared distance formed as in the density pairs and the list sorted; rho, nw and
+    count (#{r < h}, self included) are the fixed-h evaluation at that h.  status 0, or 2
+    when a periodic h reaches min(box)/2 (no density then).  Needs 2 <= k <= n.
+    """
+    lib = _load()
+    pos = _f64(pos)
+    mass = _f64(mass)
+    n = mass.shape[0]
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else tg.shape[0]
+    box = _f64(box)
+    h, rho, nw = np.empty(nt), np.empty(nt), np.empty(nt)
+    count = np.empty(nt, dtype=np.int64)
+    status = np.empty(nt, dtype=np.int32)
+    x, y, z = (np.ascontiguousarray(pos[d]) for d in range(3))
+    rc = lib.oracle_knn(n, _dp(x), _dp(y), _dp(z), _dp(mass), _dp(box), int(bool(periodic)), int(k),
+                        nt if tg is not None else -1, _ip(tg) if tg is not None else None,
+                        _MODES[mode], _dp(h), _dp(rho), _dp(nw), _ip(count), _i32p(status),
+                        KERNELS[kernel])
+    if rc == -2:
+        raise ValueError("k must lie in [2, n]")
+    if rc != 0:
+        raise MemoryError("oracle_knn failed to allocate")
+    return {"h": h, "rho": rho, "nw": nw, "count": count, "status": status}

@@ -35,6 +35,8 @@
  *      pass limit     after max_iter evaluations -> status "not converged".
  *    An unconverged particle reports the last h it was evaluated at, with the density
  *    and counts of that evaluation.
+ *  - The k-nearest-neighbour form of h (Sec. IV-C): h_i = distance to the K-th nearest
+ *    particle, rho_i by Eq. (1) at that h (oracle_knn).
  *
  * Neighbour search: a stack of uniform FP64 bucket grids (cell size box / 2^k).  For a
  * target with smoothing length h the grid with the coarsest cells no larger than h is
@@ -575,6 +577,103 @@ int oracle_batch_solve(int64_t n_groups, const int64_t *offsets, const double *x
         st->exceeded += gs.exceeded;
         st->pair_evals += gs.pair_evals;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* k-nearest-neighbour smoothing length (Sec. IV-C)                                       */
+/* ------------------------------------------------------------------------------------ */
+
+static int cmp_double(const void *a, const void *b)
+{
+    const double p = *(const double *)a, q = *(const double *)b;
+    return p < q ? -1 : p > q ? 1 : 0;
+}
+
+/* The Subfind form of the density loop (Listing 1 inside the loop of Listing 3, with the
+ * selection of Sec. IV-C): the neighbour list of a particle is put in order of distance
+ * and its first K entries are the ones that interact.  Read as a definition:
+ *   h_i   = the K-th smallest of the distances r_ij over all j, the particle itself
+ *           included (r_ii = 0 is the first), with r_ij the minimum-image distance when
+ *           periodic and r_ij^2 formed exactly as in pair();
+ *   rho_i = Eq. (1) at h = h_i; every particle with r_ij < h_i is among the K nearest and
+ *           the K-th lies at q = 1, where W = 0, so equal distances do not matter;
+ *   count_i = #{j : r_ij^2 < h_i^2}: K - 1, or more when other particles sit at distance h_i
+ *           or when h_i^2 rounds above the K-th squared distance.
+ * Every squared distance of the target is computed and the list is sorted (qsort); a
+ * periodic h_i >= min(box)/2 gets status 2 (EXCEEDS_BOX) and no density.
+ * K must lie in [2, n].  mode 0 evaluates the density with the bucket grids, mode 1 by
+ * brute force.  status_out: 0 done, 2 exceeds box. */
+int oracle_knn(int64_t n, const double *x, const double *y, const double *z, const double *m,
+               const double *box, int periodic, int k, int64_t n_targets, const int64_t *targets,
+               int mode, double *h_out, double *rho_out, double *nw_out, int64_t *count_out,
+               int32_t *status_out, int kernel)
+{
+    if (k < 2 || (int64_t)k > n) return -2;
+    pset ps;
+    setup_pset(&ps, n, x, y, z, m, box, periodic, kernel);
+    if (n_targets < 0) n_targets = n;
+    int failed = 0;
+    #pragma omp parallel
+    {
+        double *r2 = (double *)malloc((size_t)n * sizeof(double));
+        if (!r2) {
+            #pragma omp atomic write
+            failed = 1;
+        }
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < n_targets; t++) {
+            if (!r2) continue;
+            const int64_t i = targets ? targets[t] : t;
+            for (int64_t j = 0; j < n; j++) {
+                double dx = ps.x[j] - ps.x[i];
+                double dy = ps.y[j] - ps.y[i];
+                double dz = ps.z[j] - ps.z[i];
+                if (ps.periodic) {
+                    dx = min_image(dx, ps.box[0]);
+                    dy = min_image(dy, ps.box[1]);
+                    dz = min_image(dz, ps.box[2]);
+                }
+                r2[j] = dx * dx + dy * dy + dz * dz;
+            }
+            qsort(r2, (size_t)n, sizeof(double), cmp_double);
+            h_out[t] = sqrt(r2[k - 1]);
+            status_out[t] = 0;
+            if (ps.periodic) {
+                double half = 0.5 * fmin(ps.box[0], fmin(ps.box[1], ps.box[2]));
+                if (h_out[t] >= half) status_out[t] = ORC_EXCEEDS_BOX;
+            }
+        }
+        free(r2);
+    }
+    if (failed) return -1;
+    /* density at the selected h (targets whose h exceeds the box are skipped) */
+    bucket_grid grids[ORACLE_MAX_LEVEL + 1];
+    memset(grids, 0, sizeof(grids));
+    if (mode == 0) {
+        for (int64_t t = 0; t < n_targets; t++) {
+            if (status_out[t] != 0) continue;
+            int lv = level_for(&ps, h_out[t]);
+            if (!grids[lv].built && build_grid(&ps, lv, &grids[lv]) != 0) return -1;
+        }
+    }
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_targets; t++) {
+        if (status_out[t] != 0) {
+            rho_out[t] = nw_out[t] = 0.0;
+            count_out[t] = 0;
+            continue;
+        }
+        const int64_t i = targets ? targets[t] : t;
+        acc_t a;
+        double dnw;
+        if (mode == 0) eval_grid(&ps, &grids[level_for(&ps, h_out[t])], i, h_out[t], 0.0, &a);
+        else eval_brute(&ps, i, h_out[t], 0.0, &a);
+        finish(ps.kernel, h_out[t], &a, &rho_out[t], &nw_out[t], &dnw);
+        count_out[t] = a.count;
+    }
+    for (int lv = 0; lv <= ORACLE_MAX_LEVEL; lv++)
+        if (grids[lv].built) free_grid(&grids[lv]);
     return 0;
 }
 

@@ -405,3 +405,80 @@ def test_wendland_c6_solve_converges_in_band():
     r = oracle.solve(wl.pos, wl.mass, wl.h0, nngb=295.0, tol=5.0, kernel="wendland_c6")
     assert np.all(r["status"] == 0)
     assert np.all(np.abs(r["nw"] - 295.0) <= 5.0)
+
+
+# ---- k-nearest-neighbour smoothing length (Sec. IV-C) --------------------------------------
+
+def _lattice(side):
+    """Simple cubic lattice of side^3 particles with spacing a = 1/side in the unit periodic box
+    (positions are exact binary fractions, so every squared distance is exact)."""
+    a = 1.0 / side
+    g = np.arange(side) * a
+    x, y, z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()])
+    return pos, np.full(side**3, 1.0 / side**3), a
+
+
+@pytest.mark.parametrize("kernel", ["m4", "wendland_c6"])
+def test_knn_lattice_shells_closed_form(kernel):
+    # shells of the simple cubic lattice: 1 (self), 6 at a, 12 at sqrt(2) a, 8 at sqrt(3) a,
+    # 6 at 2a.  The K-th nearest distance is the shell radius holding the K-th particle, and
+    # the density sums the shells strictly inside it (the K-th shell sits at q = 1, w = 0).
+    pos, m, a = _lattice(8)
+    wfun = oracle.w if kernel == "m4" else oracle.w_c6
+    sigma = 8.0 / math.pi if kernel == "m4" else 1365.0 / (64.0 * math.pi)
+    shells = [(0.0, 1), (a, 6), (math.sqrt(2) * a, 12), (math.sqrt(3) * a, 8), (2 * a, 6)]
+    for k, hk, inner in ((2, a, 1), (7, a, 1), (8, math.sqrt(2) * a, 2), (19, math.sqrt(2) * a, 2),
+                         (20, math.sqrt(3) * a, 3), (27, math.sqrt(3) * a, 3), (33, 2 * a, 4)):
+        r = oracle.knn(pos, m, k, targets=np.arange(0, 512, 37), kernel=kernel)
+        assert np.all(r["status"] == 0)
+        np.testing.assert_allclose(r["h"], hk, rtol=2e-16)
+        rho = m[0] * sigma / hk**3 * sum(c * wfun(rad / hk) for rad, c in shells[:inner])
+        np.testing.assert_allclose(r["rho"], rho, rtol=1e-14)
+        below = sum(c for _, c in shells[:inner])
+        # the K-th shell itself is counted only if fl(h)^2 rounds above its squared radius
+        assert np.all((r["count"] == below) | (r["count"] == below + shells[inner][1]))
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_knn_matches_kdtree_kth_distance(periodic):
+    spatial = pytest.importorskip("scipy.spatial")
+    wl = inputs.make("c1", n=3000)
+    pos = wl.pos
+    tg = np.arange(0, wl.n, 7)
+    for k in (2, 33, 64, 295):
+        r = oracle.knn(pos, wl.mass, k, periodic=periodic, targets=tg)
+        tree = spatial.cKDTree(pos.T, boxsize=1.0 if periodic else None)
+        d, _ = tree.query(pos.T[tg], k=k)
+        np.testing.assert_allclose(r["h"], d[:, -1], rtol=1e-14)
+
+
+def test_knn_bracket_and_density_at_h():
+    # the K-th distance brackets the K nearest: fewer than K particles strictly closer, at
+    # least K at or within it; and the density is the fixed-h evaluation at that h
+    wl = inputs.make("c2", n=4096)
+    tg = np.arange(0, wl.n, 13)
+    k = 64
+    r = oracle.knn(wl.pos, wl.mass, k, targets=tg)
+    d = wl.pos[:, tg, None] - wl.pos[:, None, :]
+    d -= np.round(d)
+    dist = np.sqrt((d**2).sum(0))
+    assert np.all((dist < r["h"][:, None] * (1 - 1e-12)).sum(1) < k)
+    assert np.all((dist <= r["h"][:, None] * (1 + 1e-12)).sum(1) >= k)
+    e = oracle.evaluate(wl.pos, wl.mass, r["h"], targets=tg)
+    np.testing.assert_array_equal(r["rho"], e["rho"])
+    np.testing.assert_array_equal(r["count"], e["count"])
+    b = oracle.knn(wl.pos, wl.mass, k, targets=tg, mode="brute")
+    np.testing.assert_array_equal(b["h"], r["h"])
+    np.testing.assert_allclose(b["rho"], r["rho"], rtol=1e-13)
+
+
+def test_knn_exceeds_box_and_argument_range():
+    pos, m, a = _lattice(3)  # 27 particles, spacing 1/3: the 27th-nearest is at sqrt(3)/3 > 1/2
+    r = oracle.knn(pos, m, 27, targets=np.arange(3))
+    assert np.all(r["status"] == 2)
+    r = oracle.knn(pos, m, 7, targets=np.arange(3))  # 1/3 < 1/2
+    assert np.all(r["status"] == 0)
+    for k in (1, 28):
+        with pytest.raises(ValueError):
+            oracle.knn(pos, m, k)
