@@ -155,6 +155,30 @@ sph_status sph_density_solve(sph_ctx *ctx, double *h_inout_dev, double *rho_out_
 sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_dev,
                             int32_t *count_out_dev, double *nw_out_dev, double *dnw_out_dev);
 
+/* k-nearest-neighbour smoothing lengths: the Subfind form of the density loop (Sec. IV-C and
+ * Listing 3), where each particle's neighbour list is put in order of distance and its K
+ * nearest entries interact.  For every particle of the last sph_sort:
+ *   h_i     = distance to the K-th nearest particle, the particle itself counted first;
+ *   rho_i   = Eq. (1) at h_i (the K-th neighbour sits at q = 1 and adds nothing, so equal
+ *             distances do not change it);
+ *   count_i = #{j : r_ij^2 < h_i^2}: K - 1, or more when other particles sit at distance h_i
+ *             or h_i^2 rounds above the K-th squared distance;  nw_i = N_w(h_i) (nullable).
+ * h_inout_dev (n doubles, caller order): a starting search radius on entry (> 0 and below
+ * min(box)/2; it steers the passes, not the result) and h_i on exit.  Each pass keeps the
+ * squared distances inside a target's radius; with K to capacity of them (2048 in FP32,
+ * 1024 in FP64) it selects the K-th (radix select), otherwise the radius grows or shrinks
+ * (count ~ radius^3) and the target returns in the next pass, for at most max_iter passes.
+ * FP64 forms every distance exactly as the FP64 density pairs; FP32 from the FP32 offsets.
+ * Needs 2 <= k <= SPH_KNN_MAX_K and k <= n.  Returns OK; NOT_CONVERGED (passes ran out);
+ * H_EXCEEDS_BOX (the K-th distance, or the radius that would hold K particles, reaches
+ * min(box)/2); those particles report their last radius and the density there.  Errors:
+ * INVALID_ARG, NOT_SORTED, UNSUPPORTED (after sph_batch_solve), DEVICE_STATUS, CUDA.
+ * stats: passes/todo_per_pass/density_ms of the selection passes, pair_tests = candidates
+ * streamed, pair_evals = in-h pairs of the final evaluation, unconverged, exceeded. */
+#define SPH_KNN_MAX_K 512
+sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *rho_out_dev,
+                         int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats);
+
 /* Solve many independent non-periodic groups in one pass loop.  Group g owns the
  * particles [offsets[g], offsets[g+1]) of the flattened arrays; offsets_dev holds
  * n_groups + 1 int64 (offsets[0] = 0, non-decreasing); nngb_dev and tol_dev hold one

@@ -32,9 +32,11 @@ SPH_PREC_FP32_KAHAN = 1
 SPH_MAX_PASSES = 64
 
 EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sph_density_eval",
+            "sph_knn_solve",
             "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error",
             "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning", "sph_autotune")
 SPH_STATIC_MAX_PARTICLES = 32768
+SPH_KNN_MAX_K = 512
 
 
 class SphParams(ctypes.Structure):
@@ -122,6 +124,8 @@ def lib() -> ctypes.CDLL:
     L.sph_sort.argtypes = [vp, i64, vp, vp]
     L.sph_density_solve.restype = i32
     L.sph_density_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(SphStats)]
+    L.sph_knn_solve.restype = i32
+    L.sph_knn_solve.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.POINTER(SphStats)]
     L.sph_density_eval.restype = i32
     L.sph_density_eval.argtypes = [vp, vp, vp, vp, vp, vp]
     L.sph_batch_solve.restype = i32
@@ -201,6 +205,13 @@ def sph_density_solve(ctx, h_ptr: int, rho_ptr: int, count_ptr: int, nw_ptr: int
                                    ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(count_ptr or None),
                                    ctypes.c_void_p(nw_ptr or None),
                                    ctypes.byref(stats) if stats is not None else None)
+
+
+def sph_knn_solve(ctx, k: int, h_ptr: int, rho_ptr: int, count_ptr: int, nw_ptr: int = 0, stats=None) -> int:
+    return lib().sph_knn_solve(ctypes.c_void_p(ctx), int(k), ctypes.c_void_p(h_ptr or None),
+                               ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(count_ptr or None),
+                               ctypes.c_void_p(nw_ptr or None),
+                               ctypes.byref(stats) if stats is not None else None)
 
 
 def sph_density_eval(ctx, h_ptr: int, rho_ptr: int, count_ptr: int, nw_ptr: int = 0, dnw_ptr: int = 0) -> int:
@@ -327,6 +338,20 @@ class Solver:
         stats = SphStats()
         st = self._check(sph_density_solve(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
                                            nw.data_ptr(), stats),
+                         ok=(SPH_OK, SPH_ERR_NOT_CONVERGED, SPH_ERR_H_EXCEEDS_BOX))
+        return {"h": h, "rho": rho, "count": count, "nw": nw, "status": st, "stats": stats.to_dict()}
+
+    def knn(self, k, h0):
+        """k-nearest-neighbour h (distance to the k-th nearest particle) and rho there; h0 is
+        the starting search radius per particle."""
+        torch = self._torch
+        h = h0.clone()
+        rho = torch.empty_like(h)
+        nw = torch.empty_like(h)
+        count = torch.empty(self.n, dtype=torch.int32, device=h.device)
+        stats = SphStats()
+        st = self._check(sph_knn_solve(self.ctx, int(k), h.data_ptr(), rho.data_ptr(), count.data_ptr(),
+                                       nw.data_ptr(), stats),
                          ok=(SPH_OK, SPH_ERR_NOT_CONVERGED, SPH_ERR_H_EXCEEDS_BOX))
         return {"h": h, "rho": rho, "count": count, "nw": nw, "status": st, "stats": stats.to_dict()}
 

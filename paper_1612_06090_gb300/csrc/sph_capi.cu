@@ -762,6 +762,91 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
     return SPH_OK;
 }
 
+sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *rho_out_dev,
+                         int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!h_inout_dev || !rho_out_dev || !count_out_dev)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "NULL h, rho or count pointer");
+    if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
+    if (ctx->kl.seg_bits > 0)
+        return fail(ctx, SPH_ERR_UNSUPPORTED, "sph_knn_solve runs on the particles of sph_sort, not on "
+                                              "batched groups");
+    if (k < 2 || k > SPH_KNN_MAX_K || (int64_t)k > ctx->n)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "k = %d outside [2, min(%d, n = %lld)]", k, SPH_KNN_MAX_K,
+                    (long long)ctx->n);
+    if (stats) memset(stats, 0, sizeof(*stats));
+    cudaStream_t st = ctx->stream;
+    const int launches0 = ctx->launches;
+    SolveArgs a = solve_args(ctx);
+    CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
+    CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+    CU(ctx, launch_solve_init(a, h_inout_dev, ctx->params.max_iter, st), "init");
+    sph_status s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status | ctx->ds_host->sort_status)
+        return device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
+    // selection passes over the shrinking todo list
+    int cur = 0, passes_run = 0;
+    for (int pass = 0; pass < ctx->params.max_iter; pass++) {
+        a.dens_ev[0] = ctx->dev_ev[2 * pass];
+        a.dens_ev[1] = ctx->dev_ev[2 * pass + 1];
+        CU(ctx, launch_knn_pass(a, cur, k, st), "kNN pass");
+        passes_run = pass + 1;
+        CU(ctx, cudaMemcpyAsync(&ctx->ds_host->todo_count, &ctx->ds->todo_count, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st),
+           "reading the todo count");
+        CU(ctx, cudaStreamSynchronize(st), "synchronising the pass");
+        cur = 1 - cur;
+        if (ctx->ds_host->todo_count == 0) break;
+    }
+    s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    const DevState knn = *ctx->ds_host;
+    if (knn.status) return device_status_error(ctx, knn.status);
+    // one density evaluation of every particle at its selected h
+    a.dens_ev[0] = a.dens_ev[1] = nullptr;
+    CU(ctx, launch_knn_finish(a, st), "kNN finish");
+    CU(ctx, launch_pass(a, 0, false, st), "density pass");
+    CU(ctx, launch_scatter(a, h_inout_dev, rho_out_dev, count_out_dev, nw_out_dev, nullptr, st), "scatter");
+    CU(ctx, cudaEventRecord(ctx->ev[3], st), "event");
+    s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    const DevState &d = *ctx->ds_host;
+    if (d.status) return device_status_error(ctx, d.status);
+    if (stats) {
+        stats->passes = knn.pass;
+        stats->kernel_launches = ctx->launches - launches0 + ctx->sort_launches;
+        for (int q = 0; q < SPH_MAX_PASSES; q++)
+            stats->todo_per_pass[q] = q < knn.pass ? knn.todo_per_pass[q] : 0;
+        stats->unconverged = knn.todo_count;
+        stats->exceeded = knn.exceeded;
+        stats->pair_evals = (int64_t)d.pair_evals;
+        stats->pair_tests = (int64_t)knn.pair_tests;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+        stats->solve_ms = ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) stats->sort_ms = ms;
+        double kms = 0.0;
+        for (int q = 0; q < passes_run; q++) {
+            float m = 0.f;
+            if (cudaEventElapsedTime(&m, ctx->dev_ev[2 * q], ctx->dev_ev[2 * q + 1]) == cudaSuccess) {
+                kms += m;
+                stats->density_ms_per_pass[q] = m;
+            }
+        }
+        stats->density_ms = kms;
+        stats->density_launches = passes_run;
+    }
+    if (knn.exceeded > 0)
+        return fail(ctx, SPH_ERR_H_EXCEEDS_BOX, "%d particles: the K-th neighbour lies at or beyond min(box)/2",
+                    knn.exceeded);
+    if (knn.todo_count > 0)
+        return fail(ctx, SPH_ERR_NOT_CONVERGED, "%d particles without a selection after %d passes",
+                    knn.todo_count, knn.pass);
+    return SPH_OK;
+}
+
 sph_status sph_batch_solve(sph_ctx *ctx, int64_t n_groups, const int64_t *offsets_dev,
                            const double *pos_xyz_dev, const double *mass_dev, const double *nngb_dev,
                            const double *tol_dev, double *h_inout_dev, double *rho_out_dev,

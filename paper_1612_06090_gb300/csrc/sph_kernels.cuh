@@ -88,5 +88,13 @@ cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, i
 // sph_density.cu
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st);
 int density_blocks_per_sm(int precision, int direct_pct);
+// k-nearest-neighbour pass over todo (one warp per target): selects h for targets whose
+// search radius holds K..knn_capacity candidates, adapts the radius of the others
+cudaError_t launch_knn(const SolveArgs &a, const int32_t *todo, int k, cudaStream_t st);
+int knn_capacity(int precision);
+// sph_solve.cu: one kNN pass (selection + next todo list), and the switch to one density
+// evaluation of every particle at its selected h
+cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st);
+cudaError_t launch_knn_finish(const SolveArgs &a, cudaStream_t st);
 
 }  // namespace sph

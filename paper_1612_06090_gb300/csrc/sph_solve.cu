@@ -206,6 +206,27 @@ __global__ void k_scatter(SolveArgs a, double *__restrict__ h_out, double *__res
     }
 }
 
+
+// After the kNN passes: every particle is evaluated once at its selected h (the last search
+// radius for one that did not finish), as a single pass over all particles.
+__global__ void k_knn_finish(SolveArgs a)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double h = a.e_h[p];
+        a.h[p] = h;
+        a.h32[p] = (float)h;
+        a.todo[0][p] = (int32_t)p;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ds->todo_count = (int32_t)a.n;
+        a.ds->pass = 0;
+        a.ds->max_iter = 1;
+        a.ds->pair_evals = 0ull;
+        for (int k = 0; k < kMaxPasses; k++) a.ds->pairs_per_pass[k] = 0ull;
+    }
+}
+
 int blocks_for(int64_t n, int cap)
 {
     int64_t b = (n + kThreads - 1) / kThreads;
@@ -259,6 +280,31 @@ cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, i
 {
     k_scatter<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a, h_out, rho_out, count_out, nw_out,
                                                                  dnw_out);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st)
+{
+    const int32_t *todo = a.todo[cur];
+    k_pass_begin<<<1, 1, 0, st>>>(a.ds);
+    if (a.launches) *a.launches += 1;
+    if (a.dens_ev[0]) cudaEventRecord(a.dens_ev[0], st);
+    cudaError_t e = launch_knn(a, todo, k, st);
+    if (e != cudaSuccess) return e;
+    if (a.dens_ev[1]) cudaEventRecord(a.dens_ev[1], st);
+    e = compact_i32(a.flags, todo, a.todo[1 - cur], nullptr, a.n, &a.ds->pass_count, &a.ds->todo_next,
+                    a.scan_aux, a.grid_cap, st, a.launches);
+    if (e != cudaSuccess) return e;
+    k_pass_end<<<1, 1, 0, st>>>(a.ds);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_finish(const SolveArgs &a, cudaStream_t st)
+{
+    k_knn_finish<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }

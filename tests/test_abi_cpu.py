@@ -106,6 +106,7 @@ def test_calls_on_null_context(B):
     assert B.sph_density_solve(None, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
     assert B.sph_density_eval(None, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
     assert B.sph_batch_solve(None, 1, 1, 1, 1, 1, 1, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
+    assert B.sph_knn_solve(None, 64, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
     assert B.sph_set_params(None, B.make_params()) == B.SPH_ERR_INVALID_ARG
     B.sph_destroy(None)
 
