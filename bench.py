@@ -37,6 +37,10 @@ UNIT = "particles/s"
 # 3 differences, r^2 (3 mul + 2 add), 1 compare, 1 sqrt, q (1 mul), w (7), -q w' (5),
 # m*w (1), three sums (3) = 27, +1 for the integer count.
 FLOP_PER_PAIR = 28
+KNN_METRIC = "kNN SPH particles/s (h = K-th neighbour distance, rho at h)"
+# one neighbour-list entry: a squared distance from three offsets (3 subtractions, 3 multiplies,
+# 2 additions); the radius compare and the selection are not counted
+FLOP_PER_LIST_ENTRY = 8
 FP32_LANES_PER_SM = 128
 
 
@@ -56,6 +60,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
     ap.add_argument("--kernel", default="m4", choices=["m4", "c6"],
                     help="c6: the paper's Wendland C6 kernel at Nngb = 295 +- 5")
+    ap.add_argument("--knn", type=int, default=0,
+                    help="K > 0: time the k-nearest-neighbour h (sph_knn_solve) instead of the "
+                         "N_w solve; the paper's K is 295")
     return ap.parse_args()
 
 
@@ -177,11 +184,50 @@ def cpu_baseline(wl, n_targets, kernel="m4"):
             "seconds": dt, "passes": r["stats"]["passes"]}
 
 
+def cpu_baseline_knn(wl, n_targets, k, kernel="m4"):
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.default_rng(98)
+    tg = np.sort(rng.choice(wl.n, size=min(n_targets, wl.n), replace=False))
+    t0 = time.perf_counter()
+    oracle.knn(wl.pos, wl.mass, k, box=wl.box, periodic=wl.periodic, targets=tg,
+               kernel="wendland_c6" if kernel == "c6" else "m4")
+    dt = time.perf_counter() - t0
+    return {"value": len(tg) / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{len(tg):,} random targets of the same workload, K = {k}: every distance to "
+                      f"all {wl.n:,} particles sorted (qsort), then rho at h (FP64, OpenMP over "
+                      f"targets); {dt:.1f} s wall",
+            "seconds": dt}
+
+
 def run_reference(args):
     rank, world = dist_init(args)
     if rank != 0:
         return
     wl, desc = workload(args)
+    if args.knn:
+        n_t = args.cpu_sample or 1024
+        for _ in range(args.warmup):
+            cpu_baseline_knn(wl, max(64, n_t // 8), args.knn, args.kernel)
+        times, last = [], None
+        for _ in range(args.steps):
+            last = cpu_baseline_knn(wl, n_t, args.knn, args.kernel)
+            times.append(last["seconds"])
+        value = min(n_t, wl.n) / statistics.mean(times)
+        line = {
+            "impl": "reference", "metric": KNN_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": wl.n, "k": args.knn, "sample_targets": min(n_t, wl.n)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     n_t = args.cpu_sample or max(1024, wl.n // 16)
     for _ in range(args.warmup):
         cpu_baseline(wl, max(256, n_t // 8), args.kernel)
@@ -395,6 +441,174 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_knn(args):
+    """k-nearest-neighbour smoothing lengths (Sec. IV-C): one step = sort + sph_knn_solve on
+    the workload, h = distance to the K-th nearest particle and rho at that h."""
+    import numpy as np
+    import torch
+
+    from paper_1612_06090_gb300 import binding as B
+
+    rank, world = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl, desc = workload(args)
+    n, K = wl.n, args.knn
+    kern = B.SPH_KERNEL_WENDLAND_C6 if args.kernel == "c6" else B.SPH_KERNEL_M4
+    stream = torch.cuda.current_stream()
+    pos = torch.as_tensor(wl.pos, device=dev)
+    mass = torch.as_tensor(wl.mass, device=dev)
+    # starting search radius 0: the library estimates one per particle from the cell table
+    h0_np = np.zeros(n)
+    h0 = torch.as_tensor(h0_np, device=dev)
+    h = torch.empty_like(h0)
+    rho = torch.empty_like(h0)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def make(prec):
+        s = B.Solver(n, stream=stream, precision=prec, box=wl.box, nngb=max(wl.nngb, 64.0), tol=wl.tol,
+                     kernel=kern)
+        s.n = n
+        return s
+
+    def step(s, stats_out=None):
+        h.copy_(h0)
+        s._check(B.sph_sort(s.ctx, n, pos.data_ptr(), mass.data_ptr()))
+        stats = B.SphStats()
+        st = B.sph_knn_solve(s.ctx, K, h.data_ptr(), rho.data_ptr(), cnt.data_ptr(), 0, stats)
+        if st != B.SPH_OK:
+            raise B.SphError(st, B.sph_last_error(s.ctx))
+        if stats_out is not None:
+            stats_out.append(stats.to_dict())
+
+    def timed(s, steps, warmup):
+        for _ in range(warmup):
+            step(s)
+        torch.cuda.synchronize()
+        stats = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(s, stats)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [a.elapsed_time(b) for a, b in ev], stats, time.perf_counter() - w0
+
+    s32 = make(B.SPH_PREC_FP32_KAHAN)
+    with ClockSampler(local) as clk:
+        ms32, st32, wall32 = timed(s32, args.steps, args.warmup)
+    clocks = clk.summary()
+    t_max = max_over_ranks(statistics.mean(ms32), world)
+    value = world * n / (t_max / 1e3)
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    knn_ms = sum(s_["density_ms"] for s_ in st32)
+    listed = sum(s_["pair_evals"] for s_ in st32)
+    achieved = listed * FLOP_PER_LIST_ENTRY / (knn_ms / 1e3) / 1e12 if knn_ms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_knn<FP32> (neighbour lists + warp radix select)",
+            "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
+            "flop_per_list_entry": FLOP_PER_LIST_ENTRY,
+            "list_entries_per_step": listed // max(1, len(st32)),
+            "candidates_streamed_per_step": sum(s_["pair_tests"] for s_ in st32) // max(1, len(st32)),
+            "knn_ms_per_step": knn_ms / max(1, len(st32)),
+            "knn_share_of_step": knn_ms / max(1e-9, sum(ms32))}
+    launches = sum(s_["kernel_launches"] for s_ in st32)
+
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = make(B.SPH_PREC_FP64)
+        ms64, st64, _ = timed(s64, args.fp64_steps, 1)
+        t64 = max_over_ranks(statistics.mean(ms64), world)
+        r64 = s64.knn(K, h0)
+        r32 = s32.knn(K, h0)
+        h64, h32 = r64["h"].cpu().numpy(), r32["h"].cpu().numpy()
+        rho64, rho32 = r64["rho"].cpu().numpy(), r32["rho"].cpu().numpy()
+        fp64 = {"value": world * n / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64,
+                "fp32_vs_fp64": {"max_rel_h_err": float(np.max(np.abs(h32 - h64) / h64)),
+                                 "max_rel_rho_err": float(np.max(np.abs(rho32 - rho64) / rho64))}}
+        s64.close()
+
+    e2e = None
+    if not args.no_e2e:
+        hp = {"pos": torch.as_tensor(wl.pos).pin_memory(), "mass": torch.as_tensor(wl.mass).pin_memory(),
+              "h0": torch.as_tensor(h0_np).pin_memory()}
+        outp = {"h": torch.empty(n, dtype=torch.float64).pin_memory(),
+                "rho": torch.empty(n, dtype=torch.float64).pin_memory(),
+                "count": torch.empty(n, dtype=torch.int32).pin_memory()}
+        dpos, dmass, dh = torch.empty_like(pos), torch.empty_like(mass), torch.empty_like(h0)
+
+        def e2e_step():
+            dpos.copy_(hp["pos"], non_blocking=True)
+            dmass.copy_(hp["mass"], non_blocking=True)
+            dh.copy_(hp["h0"], non_blocking=True)
+            s32._check(B.sph_sort(s32.ctx, n, dpos.data_ptr(), dmass.data_ptr()))
+            st = B.sph_knn_solve(s32.ctx, K, dh.data_ptr(), rho.data_ptr(), cnt.data_ptr(), 0, None)
+            if st != B.SPH_OK:
+                raise B.SphError(st, B.sph_last_error(s32.ctx))
+            outp["h"].copy_(dh, non_blocking=True)
+            outp["rho"].copy_(rho, non_blocking=True)
+            outp["count"].copy_(cnt, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier(world)
+        te = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": world * n / te, "unit": UNIT, "ms_per_step": te * 1e3,
+               "h2d_bytes_per_step": n * (24 + 8 + 8), "d2h_bytes_per_step": n * (8 + 8 + 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_knn(wl, args.cpu_sample or 2048, K, args.kernel)
+        cpu.pop("seconds", None)
+    s32.close()
+    if rank == 0:
+        st0 = st32[-1]
+        line = {
+            "metric": KNN_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "k": K,
+                       "precision": "FP32 squared distances and radix select, FP32+Kahan density at h",
+                       "start": "search radii estimated from the cell table (h_in = 0)",
+                       "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "selection_passes": st0["passes"], "todo_per_pass": st0["todo_per_pass"],
+                       "sort_ms": st0["sort_ms"], "solve_ms": st0["solve_ms"],
+                       "list_entries_per_pass": st0["pairs_per_pass"],
+                       "knn_ms_per_pass": [round(v, 3) for v in st0["density_ms_per_pass"]],
+                       "wall_s_timed_region": wall32},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
 def profiled_traffic():
     """Mean DRAM bytes per density launch from the committed ncu summary, valid only while the
     kernel sources are the ones that summary was captured from (else None)."""
@@ -578,6 +792,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.knn:
+        run_knn(args)
     elif args.config == "c4":
         run_batch(args)
     elif args.config == "c5":

@@ -163,18 +163,21 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
  *             distances do not change it);
  *   count_i = #{j : r_ij^2 < h_i^2}: K - 1, or more when other particles sit at distance h_i
  *             or h_i^2 rounds above the K-th squared distance;  nw_i = N_w(h_i) (nullable).
- * h_inout_dev (n doubles, caller order): a starting search radius on entry (> 0 and below
- * min(box)/2; it steers the passes, not the result) and h_i on exit.  Each pass keeps the
- * squared distances inside a target's radius; with K to capacity of them (2048 in FP32,
- * 1024 in FP64) it selects the K-th (radix select), otherwise the radius grows or shrinks
- * (count ~ radius^3) and the target returns in the next pass, for at most max_iter passes.
+ * h_inout_dev (n doubles, caller order): a starting search radius on entry (below min(box)/2;
+ * it steers the passes, not the result), or <= 0 to have one estimated from the local cell
+ * density; h_i on exit.  Each pass streams a target's candidates inside its radius through
+ * a per-warp buffer of 1024 squared distances that is cut back to its
+ * K nearest whenever it would overflow; with at least K inside the radius the K-th is
+ * selected (radix select), otherwise the radius grows (count ~ radius^3) and the target
+ * returns in the next pass, for at most max_iter passes.
  * FP64 forms every distance exactly as the FP64 density pairs; FP32 from the FP32 offsets.
  * Needs 2 <= k <= SPH_KNN_MAX_K and k <= n.  Returns OK; NOT_CONVERGED (passes ran out);
  * H_EXCEEDS_BOX (the K-th distance, or the radius that would hold K particles, reaches
  * min(box)/2); those particles report their last radius and the density there.  Errors:
  * INVALID_ARG, NOT_SORTED, UNSUPPORTED (after sph_batch_solve), DEVICE_STATUS, CUDA.
  * stats: passes/todo_per_pass/density_ms of the selection passes, pair_tests = candidates
- * streamed, pair_evals = in-h pairs of the final evaluation, unconverged, exceeded. */
+ * streamed, pair_evals / pairs_per_pass = neighbour-list entries (squared distances inside
+ * the search radius) built by the selection passes, unconverged, exceeded. */
 #define SPH_KNN_MAX_K 512
 sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *rho_out_dev,
                          int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats);

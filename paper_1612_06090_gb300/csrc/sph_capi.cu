@@ -781,7 +781,7 @@ sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *r
     SolveArgs a = solve_args(ctx);
     CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
     CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
-    CU(ctx, launch_solve_init(a, h_inout_dev, ctx->params.max_iter, st), "init");
+    CU(ctx, launch_knn_init(a, h_inout_dev, ctx->params.max_iter, k, st), "init");
     sph_status s = read_state(ctx);
     if (s != SPH_OK) return s;
     if (ctx->ds_host->status | ctx->ds_host->sort_status)
@@ -821,8 +821,10 @@ sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *r
             stats->todo_per_pass[q] = q < knn.pass ? knn.todo_per_pass[q] : 0;
         stats->unconverged = knn.todo_count;
         stats->exceeded = knn.exceeded;
-        stats->pair_evals = (int64_t)d.pair_evals;
+        stats->pair_evals = (int64_t)knn.pair_evals;
         stats->pair_tests = (int64_t)knn.pair_tests;
+        for (int q = 0; q < SPH_MAX_PASSES; q++)
+            stats->pairs_per_pass[q] = q < knn.pass ? (int64_t)knn.pairs_per_pass[q] : 0;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
         stats->solve_ms = ms;

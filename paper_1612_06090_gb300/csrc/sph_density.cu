@@ -830,22 +830,25 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
 //
 // The Subfind form of the density loop orders each particle's neighbour list by distance and
 // keeps the K nearest.  Here one warp owns one target: it streams the candidates inside the
-// target's current search radius H (the same culled cell stream as the density pass), keeps
-// their squared distances in a per-warp buffer, and when K <= count <= capacity selects the
-// K-th smallest with a warp radix select (8-bit digits on the IEEE bit patterns, which order
-// non-negative floats).  h = sqrt of that value.  Otherwise H grows or shrinks (towards the
-// geometric middle of [K, capacity], or by halving the bracket once a radius with too few and
-// one with too many are known) and the target returns in the next pass.
+// target's current search radius H (the same culled cell stream as the density pass) and keeps
+// their squared distances in a per-warp buffer, cut back to its K nearest whenever it would
+// overflow.  With at least K candidates inside H the K-th smallest is selected with a warp radix
+// select (8-bit digits on the IEEE bit patterns, which order non-negative floats); h = sqrt of
+// it.  With fewer, H grows and the target returns in the next pass.
 // FP32: squared distances of the FP32 offsets, as in the FP32 density pairs.  FP64: formed
 // from the FP64 positions exactly as the FP64 pairs (and the oracle) form them.
 
 constexpr int kKnnWarps = 8;
 constexpr int kKnnThreads = 32 * kKnnWarps;
-constexpr int kKnnBufBytes = 8192;
-constexpr int kKnnWarpBytes = kKnnBufBytes + 256 * 4 + 2 * kMaxCells * 4;
+constexpr int kKnnCap = 1024;  // buffered squared distances per warp (SPH_KNN_MAX_K = cap / 2)
+constexpr int kKnnLoads = 4;   // independent candidate loads per lane per stream round
 
 template <bool kF64>
-__host__ __device__ constexpr int knn_cap() { return kKnnBufBytes / (kF64 ? 8 : 4); }
+__host__ __device__ constexpr int knn_cap() { return kKnnCap; }
+template <bool kF64>
+__host__ __device__ constexpr int knn_buf_bytes() { return kKnnCap * (kF64 ? 8 : 4); }
+template <bool kF64>
+__host__ __device__ constexpr int knn_warp_bytes() { return knn_buf_bytes<kF64>() + 256 * 4 + 2 * kMaxCells * 4; }
 
 // K-th smallest (1-based) of the c keys; every round keeps the keys that agree with the digits
 // chosen so far and histograms their next digit.
@@ -898,7 +901,7 @@ __device__ __forceinline__ U radix_select(const U *__restrict__ keys, int c, int
 }
 
 template <bool kF64>
-__global__ void __launch_bounds__(kKnnThreads, 2)
+__global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
     k_knn(SolveArgs a, const int32_t *__restrict__ todo, int K)
 {
     using T = typename std::conditional<kF64, double, float>::type;
@@ -906,14 +909,15 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
     constexpr int cap = knn_cap<kF64>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wb = smem + (size_t)warp * kKnnWarpBytes;
+    unsigned char *wb = smem + (size_t)warp * knn_warp_bytes<kF64>();
     T *buf = (T *)wb;
-    int *hist = (int *)(wb + kKnnBufBytes);
+    int *hist = (int *)(wb + knn_buf_bytes<kF64>());
     int *cpre = hist + 256;
     int *cbeg = cpre + kMaxCells;
     const int n_todo = a.ds->pass_count;
+    const int pass = a.ds->pass;
     int exceeded = 0;
-    unsigned long long tests = 0;
+    unsigned long long tests = 0, listed = 0;
 
     for (;;) {
         int t = 0;
@@ -964,9 +968,21 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
             __syncwarp();
         }
         int cc = 0, coff = cbeg[0], cnxt = cpre[1];
-        int c = 0;  // candidates strictly inside H (all of them, also past the buffer)
-        for (int base = 0; base < total; base += 32) {
-            const int f = base + lane;
+        // The buffer holds candidates inside H.  When it would overflow it is cut to the
+        // entries at or below its K-th smallest value tau; from then on only candidates at or
+        // below tau enter (tau only falls, so every value below the final tau stays, and the
+        // K-th smallest of the buffer at the end is the K-th smallest inside H).
+        int seen = 0;  // candidates strictly inside H
+        int c = 0;     // entries in the buffer
+        bool cut = false, stuck = false;
+        T tau = 0;
+        for (int base = 0; base < total; base += 32 * kKnnLoads) {
+          // the round's loads are all issued before any is used
+          int jj[kKnnLoads];
+          uint4 PP[kKnnLoads];
+#pragma unroll
+          for (int u = 0; u < kKnnLoads; u++) {
+            const int f = base + 32 * u + lane;
             if (f < total && cnxt <= f) {
                 int ci = cc;
 #pragma unroll
@@ -976,13 +992,22 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
                 coff = cbeg[ci] - cpre[ci];
                 cnxt = ci + 1 < kMaxCells ? cpre[ci + 1] : INT_MAX;
             }
-            const int j = f < total ? f + coff : -1;
+            jj[u] = f < total ? f + coff : -1;
+            PP[u] = make_uint4(0, 0, 0, 0);
+            if (jj[u] >= 0) PP[u] = a.pfix[jj[u]];
+          }
+#pragma unroll
+          for (int u = 0; u < kKnnLoads; u++) {
+            const int j = jj[u];
             bool in = false;
             T r2 = 0;
             if (j >= 0) {
-                const uint4 Pj = a.pfix[j];
-                int rj[3];
-                if (in_query(G3, Pj, rj)) {
+                // one target: its offsets are wrapped minimum images, and a candidate outside
+                // the query box also fails the radius test, so no box test is needed
+                const uint4 Pj = PP[u];
+                const int rj[3] = {(int32_t)(Pj.x - G3.X0[0]), (int32_t)(Pj.y - G3.X0[1]),
+                                   (int32_t)(Pj.z - G3.X0[2])};
+                {
                     const float fx = (float)rj[0] * qf[0], fy = (float)rj[1] * qf[1],
                                 fz = (float)rj[2] * qf[2];
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
@@ -1008,18 +1033,46 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
                     }
                 }
             }
-            const unsigned m = __ballot_sync(kFull, in);
-            if (in) {
-                const int slot = c + __popc(m & lanemask_lt());
-                if (slot < cap) buf[slot] = r2;
+            seen += __popc(__ballot_sync(kFull, in));
+            bool keep = in && (!cut || r2 <= tau);
+            unsigned m = __ballot_sync(kFull, keep);
+            if (c + __popc(m) > cap && !stuck) {
+                const U kth = radix_select<U>((const U *)buf, c, K, hist);
+                memcpy(&tau, &kth, sizeof(T));
+                cut = true;
+                int nc = 0;
+                for (int i0 = 0; i0 < c; i0 += 32) {
+                    const int i = i0 + lane;
+                    T v = 0;
+                    bool kp = false;
+                    if (i < c) {
+                        v = buf[i];
+                        kp = v <= tau;
+                    }
+                    __syncwarp();  // the round's reads come before any of its writes
+                    const unsigned km = __ballot_sync(kFull, kp);
+                    if (kp) buf[nc + __popc(km & lanemask_lt())] = v;
+                    nc += __popc(km);
+                    __syncwarp();
+                }
+                c = nc;
+                // more than cap - 32 entries equal tau: no room can be made (handled below)
+                stuck = c + 32 > cap;
+                keep = in && r2 <= tau;
+                m = __ballot_sync(kFull, keep);
             }
-            c += __popc(m);
+            if (!stuck) {
+                if (keep) buf[c + __popc(m & lanemask_lt())] = r2;
+                c += __popc(m);
+            }
+          }
         }
         tests += (unsigned long long)total;
+        listed += (unsigned long long)seen;
         __syncwarp();
 
         int alive = 0;
-        if (c >= K && c <= cap) {
+        if (seen >= K && !stuck) {
             const U key = radix_select<U>((const U *)buf, c, K, hist);
             T r2k;
             memcpy(&r2k, &key, sizeof(T));
@@ -1031,21 +1084,20 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
                 a.e_h[p] = h;
             }
         } else {
-            // bracket: lo holds fewer than K candidates, hi more than cap.  With one side known
-            // the count is taken to grow as H^3 and H aims at the geometric middle of [K, cap];
-            // with both, the bracket is halved geometrically (the count is monotone in H, so
-            // this ends even where density changes steeply)
+            // bracket: lo holds fewer than K candidates, hi a radius where the buffer could not
+            // be cut.  Growing, the count is taken to scale as H^3 and H aims at 2K candidates;
+            // with both sides known the bracket is halved geometrically (the count is monotone
+            // in H, so this ends even where density changes steeply)
             double lo = a.hlo[p], hi = a.hhi[p];
-            if (c < K) lo = H;
-            else hi = H;
+            if (seen < K) lo = H;
+            else hi = H;  // stuck: thousands of equal distances inside H
             double hn;
             if (lo > 0.0 && hi < HUGE_VAL) {
                 hn = sqrt(lo * hi);
+            } else if (seen < K) {
+                hn = H * fmin(fmax(cbrt(2.0 * K / (double)(seen > 0 ? seen : 1)), 1.05), 4.0);
             } else {
-                const double aim = sqrt((double)K * (double)cap);
-                double f = cbrt(aim / (double)(c > 0 ? c : 1));
-                f = c < K ? fmin(fmax(f, 1.05), 4.0) : fmax(fmin(f, 0.95), 0.25);
-                hn = H * f;
+                hn = H * 0.5;
             }
             if (lane == 0) {
                 a.hlo[p] = lo;
@@ -1073,6 +1125,10 @@ __global__ void __launch_bounds__(kKnnThreads, 2)
     if (lane == 0) {
         if (exceeded) atomicAdd(&a.ds->exceeded, exceeded);
         if (tests) atomicAdd(&a.ds->pair_tests, tests);
+        if (listed) {
+            atomicAdd(&a.ds->pair_evals, listed);
+            if (pass < kMaxPasses) atomicAdd(&a.ds->pairs_per_pass[pass], listed);
+        }
     }
 }
 
@@ -1124,7 +1180,7 @@ cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t
 template <bool kF64>
 int knn_blocks_per_sm()
 {
-    const int bytes = kKnnWarps * kKnnWarpBytes;
+    const int bytes = kKnnWarps * knn_warp_bytes<kF64>();
     cudaFuncSetAttribute(k_knn<kF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_knn<kF64>, kKnnThreads, bytes);
@@ -1138,11 +1194,12 @@ cudaError_t launch_knn(const SolveArgs &a, const int32_t *todo, int k, cudaStrea
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int bytes = kKnnWarps * kKnnWarpBytes;
     if (a.precision == 0)
-        k_knn<true><<<sms * knn_blocks_per_sm<true>(), kKnnThreads, bytes, st>>>(a, todo, k);
+        k_knn<true><<<sms * knn_blocks_per_sm<true>(), kKnnThreads, kKnnWarps * knn_warp_bytes<true>(), st>>>(
+            a, todo, k);
     else
-        k_knn<false><<<sms * knn_blocks_per_sm<false>(), kKnnThreads, bytes, st>>>(a, todo, k);
+        k_knn<false><<<sms * knn_blocks_per_sm<false>(), kKnnThreads, kKnnWarps * knn_warp_bytes<false>(),
+                       st>>>(a, todo, k);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }

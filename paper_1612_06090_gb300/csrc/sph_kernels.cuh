@@ -96,5 +96,7 @@ int knn_capacity(int precision);
 // evaluation of every particle at its selected h
 cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st);
 cudaError_t launch_knn_finish(const SolveArgs &a, cudaStream_t st);
+// starting radii of the kNN passes (entries <= 0 are estimated from the cell tables)
+cudaError_t launch_knn_init(const SolveArgs &a, const double *h_in, int max_iter, int k, cudaStream_t st);
 
 }  // namespace sph

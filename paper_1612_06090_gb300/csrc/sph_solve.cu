@@ -42,6 +42,25 @@ __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
     big = S.periodic && ((float)(1ll << (cb - l)) + hu >= (float)(1ll << (cb - 1)));
 }
 
+__device__ void reset_state(DevState *ds, int64_t n, int max_iter)
+{
+    ds->todo_count = (int32_t)n;
+    ds->todo_next = 0;
+    ds->n_items = 0;
+    ds->item_head = 0;
+    ds->exceeded = 0;
+    ds->pass = 0;
+    ds->max_iter = max_iter;
+    ds->loop_flag = n > 0 ? 1 : 0;
+    ds->pass_count = 0;
+    ds->pair_evals = 0ull;
+    ds->pair_tests = 0ull;
+    for (int k = 0; k < kMaxPasses; k++) {
+        ds->todo_per_pass[k] = 0;
+        ds->pairs_per_pass[k] = 0ull;
+    }
+}
+
 __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int max_iter)
 {
     const int64_t n = a.n;
@@ -60,23 +79,53 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
         a.todo[0][p] = (int32_t)p;
     }
     if (bad) atomicOr(&a.ds->status, bad);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ds->todo_count = (int32_t)n;
-        a.ds->todo_next = 0;
-        a.ds->n_items = 0;
-        a.ds->item_head = 0;
-        a.ds->exceeded = 0;
-        a.ds->pass = 0;
-        a.ds->max_iter = max_iter;
-        a.ds->loop_flag = n > 0 ? 1 : 0;
-        a.ds->pass_count = 0;
-        a.ds->pair_evals = 0ull;
-        a.ds->pair_tests = 0ull;
-        for (int k = 0; k < kMaxPasses; k++) {
-            a.ds->todo_per_pass[k] = 0;
-            a.ds->pairs_per_pass[k] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_state(a.ds, n, max_iter);
+}
+
+// Starting search radii of the kNN passes.  A caller radius <= 0 is replaced by an estimate:
+// the particle's cell at the dense-table level, widened to coarser levels until it holds 32
+// particles, gives a local number density, and the radius is the one whose ball would hold 1.5K
+// particles at that density (capped below half the periodic box).  The radius only steers the
+// passes; the selected h does not depend on it.
+__global__ void k_knn_init(SolveArgs a, const double *__restrict__ h_in, int max_iter, int K)
+{
+    const int64_t n = a.n;
+    int bad = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = a.idx[p];
+        const uint64_t key = a.key[p];
+        const SegInfo &S = a.segs[seg_of(key, a.kl)];
+        double hv = h_in[i];
+        if (hv <= 0.0) {
+            const int32_t *t = a.ctab + S.tab_off;
+            const int lc = S.level_c;
+            const uint64_t local = key & ((1ull << (3 * a.kl.lmax)) - 1ull);
+            uint64_t m = local >> (3 * (a.kl.lmax - lc));
+            int l = lc;
+            int64_t cnt = (int64_t)t[m + 1] - t[m];
+            while (cnt < 32 && l > 0) {
+                l--;
+                m >>= 3;
+                const int sh = 3 * (lc - l);
+                cnt = (int64_t)t[(m + 1) << sh] - t[m << sh];
+            }
+            double vol = 1.0;
+            for (int d = 0; d < 3; d++) vol *= ldexp(S.q[d], a.kl.coord_bits - l);
+            const double dens = (double)(cnt > 0 ? cnt : 1) / vol;
+            hv = cbrt(3.0 * (1.5 * K) / (4.0 * 3.14159265358979323846 * dens));
+            if (S.periodic) hv = fmin(hv, 0.999 * S.half_box);
         }
+        if (!(hv > 0.0 && hv <= DBL_MAX) || (S.periodic && hv >= S.half_box)) bad |= kBadH;
+        a.h[p] = hv;
+        a.h32[p] = (float)hv;
+        a.hlo[p] = 0.0;
+        a.hhi[p] = HUGE_VAL;
+        a.e_h[p] = hv;
+        a.todo[0][p] = (int32_t)p;
     }
+    if (bad) atomicOr(&a.ds->status, bad);
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_state(a.ds, n, max_iter);
 }
 
 // A pass evaluates pass_count entries: the whole todo list while the loop runs, none once it
@@ -298,6 +347,13 @@ cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st)
                     a.scan_aux, a.grid_cap, st, a.launches);
     if (e != cudaSuccess) return e;
     k_pass_end<<<1, 1, 0, st>>>(a.ds);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_knn_init(const SolveArgs &a, const double *h_in, int max_iter, int k, cudaStream_t st)
+{
+    k_knn_init<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a, h_in, max_iter, k);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }

@@ -55,8 +55,9 @@ def check_fp32(g, pos, mass, tg, k, o, kernel="m4"):
 def test_knn_fp64_bit_exact(cfg, n, k):
     wl = inputs.make(cfg, n=n)
     rng = np.random.default_rng(k)
-    # starting radii from far too small to far too large: only the number of passes changes
-    h0 = wl.h0 * rng.choice([0.3, 1.0, 3.0], size=wl.n)
+    # starting radii from far too small to far too large, and 0 (estimated from the local cell
+    # density): only the number of passes changes
+    h0 = wl.h0 * rng.choice([0.0, 0.3, 1.0, 3.0], size=wl.n)
     g = gpu_knn(wl.pos, wl.mass, k, h0, FP64)
     assert g["status"] == B.SPH_OK
     assert g["stats"]["unconverged"] == 0
@@ -145,16 +146,27 @@ def test_knn_argument_errors():
     for k in (1, 0, B.SPH_KNN_MAX_K + 1, wl.n + 1):
         assert B.sph_knn_solve(s.ctx, k, h.data_ptr(), rho.data_ptr(), cnt.data_ptr()) == B.SPH_ERR_INVALID_ARG
     assert B.sph_knn_solve(s.ctx, 64, 0, rho.data_ptr(), cnt.data_ptr()) == B.SPH_ERR_INVALID_ARG
-    bad = torch.full_like(h, -1.0)
-    assert B.sph_knn_solve(s.ctx, 64, bad.data_ptr(), rho.data_ptr(), cnt.data_ptr()) == B.SPH_ERR_DEVICE_STATUS
+    for v in (float("nan"), float("inf"), 0.5):  # not a radius, or not below half the box
+        bad = torch.full_like(h, v)
+        assert B.sph_knn_solve(s.ctx, 64, bad.data_ptr(), rho.data_ptr(), cnt.data_ptr()) == B.SPH_ERR_DEVICE_STATUS
     s.close()
 
 
+def test_knn_estimated_radius_fp32():
+    # every starting radius estimated from the cell table (the bench's start)
+    wl = inputs.make("c2", n=16384)
+    g = gpu_knn(wl.pos, wl.mass, 295, 0.0, FP32)
+    assert g["status"] == B.SPH_OK
+    tg = np.arange(0, wl.n, 5)
+    check_fp32(g, wl.pos, wl.mass, tg, 295, oracle.knn(wl.pos, wl.mass, 295, targets=tg))
+
+
 def test_knn_full_size_c2_sampled():
-    # the 1,048,576-particle Plummer-cluster workload at the paper's K = 295, FP32 (the bench
-    # launch configuration), checked on sampled targets against the oracle's full sort
+    # the 1,048,576-particle Plummer-cluster workload at the paper's K = 295, FP32 with the
+    # radii estimated from the cell table (the bench launch configuration), checked on sampled
+    # targets against the oracle's full sort
     wl = inputs.make("c2")
-    g = gpu_knn(wl.pos, wl.mass, 295, wl.h0 * (295.0 / 64.0) ** (1 / 3), FP32)
+    g = gpu_knn(wl.pos, wl.mass, 295, 0.0, FP32)
     assert g["status"] == B.SPH_OK
     rng = np.random.default_rng(295)
     tg = np.sort(rng.choice(wl.n, size=96, replace=False))
