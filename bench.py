@@ -618,7 +618,7 @@ def profiled_traffic():
     try:
         text = open(os.path.join(ROOT, "profiles", "density_fp32_c2_1M.md")).read()
         src = b"".join(open(os.path.join(ROOT, "paper_1612_06090_gb300", "csrc", f), "rb").read()
-                       for f in ("sph_density.cu", "sph_common.cuh", "sph_kernels.cuh"))
+                       for f in ("sph_density.cu", "sph_items.cuh", "sph_common.cuh"))
         want = re.search(r"kernel_source_sha256_16: (\w+)", text).group(1)
         if hashlib.sha256(src).hexdigest()[:16] != want:
             return None

@@ -21,9 +21,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libsph.so")
 
-SOURCES = ["sph_scan.cu", "sph_sort.cu", "sph_density.cu", "sph_solve.cu", "sph_capi.cu",
+SOURCES = ["sph_scan.cu", "sph_sort.cu", "sph_density.cu", "sph_knn.cu", "sph_solve.cu", "sph_capi.cu",
            "sph_static_eval.cu"]
-HEADERS = [os.path.join(CSRC, h) for h in ("sph_common.cuh", "sph_kernels.cuh")] + [
+HEADERS = [os.path.join(CSRC, h) for h in ("sph_common.cuh", "sph_kernels.cuh", "sph_items.cuh")] + [
     os.path.join(INCLUDE, "sph.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

@@ -21,9 +21,8 @@
 // written (IEEE roundings, no contraction), so neighbour sets and per-pair terms are the
 // FP64 ones.
 #include <climits>
-#include <cstring>
-#include <type_traits>
 
+#include "sph_items.cuh"
 #include "sph_kernels.cuh"
 
 namespace sph {
@@ -36,7 +35,6 @@ constexpr int kStage = 256;            // candidates staged per warp before a pa
 constexpr int kStageCap = kStage + 32; // + room to pad the stage to a multiple of 32
 constexpr int kRing = 32;              // per-lane queue of in-h pairs (power of two)
 constexpr int kSubSteps = 16;          // tests per lane between drains (<= kRing / 2)
-constexpr int kMaxCells = 64;          // cells per item (4 per dimension)
 constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ float sqrt_approx(float x)
@@ -53,179 +51,6 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
     float t = __fadd_rn(s, y);
     c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
-}
-
-__device__ __forceinline__ int64_t lower_bound_key(const uint64_t *__restrict__ key, int64_t lo,
-                                                   int64_t hi, uint64_t k)
-{
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (key[mid] < k) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Particle range [s, e) of the level-l cell with Morton code m in segment g.
-__device__ __forceinline__ int2 cell_range(uint64_t m, int l, int g, const SegInfo &S,
-                                           const KeyLayout &kl, const int32_t *__restrict__ ctab,
-                                           const uint64_t *__restrict__ key)
-{
-    const int32_t *t = ctab + S.tab_off;
-    const int lc = S.level_c;
-    if (l <= lc) {
-        const int sh = 3 * (lc - l);
-        return make_int2(t[m << sh], t[(m + 1) << sh]);
-    }
-    const uint64_t anc = m >> (3 * (l - lc));
-    int64_t lo = t[anc], hi = t[anc + 1];
-    const uint64_t base = kl.seg_bits > 0 ? ((uint64_t)g << (3 * kl.lmax)) : 0ull;
-    const int sh = 3 * (kl.lmax - l);
-    const uint64_t k0 = base + (m << sh);
-    const uint64_t k1 = base + ((m + 1) << sh);
-    int64_t s = lower_bound_key(key, lo, hi, k0);
-    int64_t e = lower_bound_key(key, s, hi, k1);
-    return make_int2((int)s, (int)e);
-}
-
-// Warp-uniform geometry of one work item.
-struct ItemGeom {
-    uint32_t X0[3];   // fixed-point position of the first target
-    int64_t lo[3];    // query box relative to X0, inclusive
-    int64_t hi[3];
-    int qlo[3];       // the same bounds clamped to int32 (whole range for full dimensions),
-    int qhi[3];       // which is all the per-candidate test needs
-    int bmin[3];      // bounding box of the item's targets relative to X0
-    int bmax[3];
-    float hmax;       // largest h of the item's targets
-    int full[3];      // periodic dimension covered entirely
-    int level;        // enumeration level
-    uint32_t c_lo[3]; // first cell per dimension
-    int nc[3];        // cells per dimension
-    int64_t cstart[3];  // start of the first cell relative to X0 (fixed point; non-full dims)
-};
-
-// All item geometry is bounds for culling, so it is computed in FP32 with margins that
-// only ever enlarge it (FP64 arithmetic runs at a small fraction of the FP32 rate here).
-__device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl, int cell_div,
-                                           bool active, const uint4 &P, float hf, ItemGeom &G,
-                                           int rel[3])
-{
-    const uint32_t pc[3] = {P.x, P.y, P.z};
-    // h > 0, so the order of the float bit patterns is the order of the values
-    const float hmax = __int_as_float(__reduce_max_sync(kFull, active ? __float_as_int(hf) : 0));
-    const int cb = kl.coord_bits;
-    const int64_t range = 1ll << cb;
-    int64_t E = 0;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        G.X0[d] = __shfl_sync(kFull, pc[d], 0);
-        rel[d] = (int32_t)(pc[d] - G.X0[d]);
-        const int bmin = __reduce_min_sync(kFull, active ? rel[d] : INT_MAX);
-        const int bmax = __reduce_max_sync(kFull, active ? rel[d] : INT_MIN);
-        G.bmin[d] = bmin;
-        G.bmax[d] = bmax;
-        const int64_t H =
-            (int64_t)fminf(ceilf(hmax * (float)S.inv_q[d] * (1.0f + 1.0f / 1048576.0f)) + 2.0f, 4.0e18f);
-        G.lo[d] = (int64_t)bmin - H;
-        G.hi[d] = (int64_t)bmax + H;
-        // A periodic dimension whose query spans half the range or more is taken whole
-        // (each cell once); below that the cells it meets are counted modulo 2^level.
-        G.full[d] = S.periodic && (G.hi[d] - G.lo[d] + 1 >= range / 2);
-        const int64_t ext = G.full[d] ? range : G.hi[d] - G.lo[d] + 1;
-        E = ext > E ? ext : E;
-        G.qlo[d] = G.full[d] ? INT_MIN : (int)(G.lo[d] < INT_MIN ? (int64_t)INT_MIN : G.lo[d]);
-        G.qhi[d] = G.full[d] ? INT_MAX : (int)(G.hi[d] > INT_MAX ? (int64_t)INT_MAX : G.hi[d]);
-    }
-    G.hmax = hmax;
-    // cells of at least E / cell_div: at most cell_div + 1 cells per dimension meet the query
-    int l = kl.lmax;
-    while (l > 0 && cell_div * (1ll << (cb - l)) < E) l--;
-    if (S.periodic && l == 0) l = 1;  // keep shifts below 32; the level-1 cells cover the box
-    G.level = l;
-    const int s = cb - l;
-    const uint32_t cmask = (uint32_t)((1ull << l) - 1);
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        if (G.full[d]) {
-            G.c_lo[d] = 0;
-            G.nc[d] = 1 << l;
-            G.cstart[d] = 0;
-        } else if (S.periodic) {
-            const uint32_t alo = G.X0[d] + (uint32_t)G.lo[d];
-            const uint32_t ahi = G.X0[d] + (uint32_t)G.hi[d];
-            G.c_lo[d] = alo >> s;
-            G.nc[d] = (int)((((ahi >> s) - (alo >> s)) & cmask) + 1);
-            G.cstart[d] = G.lo[d] - (int64_t)(alo & ((1u << s) - 1u));
-        } else {
-            int64_t alo = (int64_t)G.X0[d] + G.lo[d];
-            int64_t ahi = (int64_t)G.X0[d] + G.hi[d];
-            if (alo < 0) alo = 0;
-            if (ahi > 2147483647ll) ahi = 2147483647ll;
-            G.c_lo[d] = (uint32_t)(alo >> s);
-            G.nc[d] = ahi >= alo ? (int)((ahi >> s) - (alo >> s) + 1) : 0;
-            G.cstart[d] = ((alo >> s) << s) - (int64_t)G.X0[d];
-        }
-    }
-}
-
-// Ranges of the item's cells; lane holds cells `lane` and `lane + 32`.  A cell that lies
-// entirely outside the staging ball (centre cc, squared radius ball2, both in the FP32 offset
-// units of the item) can hold no candidate, so its range is left empty: no lookup, no loads.
-// The test only drops cells whose nearest point is farther than the ball radius by a
-// relative 1e-4, far above the rounding of the FP32 cell bounds (a few 1e-7 of the extent).
-__device__ __forceinline__ void item_ranges(const ItemGeom &G, int g, const SegInfo &S,
-                                            const KeyLayout &kl, const int32_t *__restrict__ ctab,
-                                            const uint64_t *__restrict__ key, int ncell,
-                                            const float cc[3], float ball2, const float qf[3],
-                                            long long r[2])
-{
-    const int lane = lane_id();
-    const uint32_t cmask = (uint32_t)((1ull << G.level) - 1);
-    // first cell's start and the cell size per dimension in FP32 offset units (warp-uniform)
-    float c0f[3], csf[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        csf[d] = (float)(1ll << (kl.coord_bits - G.level)) * qf[d];
-        c0f[d] = (float)G.cstart[d] * qf[d];
-    }
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int c = lane + 32 * k;
-        r[k] = 0;
-        if (c < ncell) {
-            const int ix = c % G.nc[0];
-            const int iy = (c / G.nc[0]) % G.nc[1];
-            const int iz = c / (G.nc[0] * G.nc[1]);
-            const int id[3] = {ix, iy, iz};
-            float dist2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                if (G.full[d]) continue;
-                const float flo = fmaf((float)id[d], csf[d], c0f[d]), fhi = flo + csf[d];
-                const float dd = fmaxf(fmaxf(flo - cc[d], cc[d] - fhi), 0.f);
-                dist2 = fmaf(dd, dd, dist2);
-            }
-            if (dist2 > ball2 * 1.0001f) continue;
-            const uint32_t cx = (G.c_lo[0] + ix) & cmask;
-            const uint32_t cy = (G.c_lo[1] + iy) & cmask;
-            const uint32_t cz = (G.c_lo[2] + iz) & cmask;
-            const int2 se = cell_range(morton3(cx, cy, cz), G.level, g, S, kl, ctab, key);
-            r[k] = (long long)(unsigned)se.x | ((long long)se.y << 32);
-        }
-    }
-}
-
-__device__ __forceinline__ bool in_query(const ItemGeom &G, const uint4 &Pj, int rj[3])
-{
-    const uint32_t pc[3] = {Pj.x, Pj.y, Pj.z};
-    bool in = true;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        rj[d] = (int32_t)(pc[d] - G.X0[d]);
-        in = in && rj[d] >= G.qlo[d] && rj[d] <= G.qhi[d];
-    }
-    return in;
 }
 
 struct Acc32 {
@@ -292,14 +117,6 @@ __device__ __forceinline__ void pair32(float2 e, float hinv2, Acc32 &A)
 }
 
 // ---- FP64 pair terms, written as the FP64 reference writes them --------------------------
-__device__ __forceinline__ double min_image64(double dx, double L)
-{
-    const double half = __dmul_rn(0.5, L);
-    if (dx > half) return __dsub_rn(dx, L);
-    if (dx < -half) return __dadd_rn(dx, L);
-    return dx;
-}
-
 __device__ __forceinline__ double w64(double q)
 {
     if (q <= 0.5) {
@@ -826,312 +643,6 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
 }
 
 
-// ---- k-nearest-neighbour smoothing length (Sec. IV-C) --------------------------------------
-//
-// The Subfind form of the density loop orders each particle's neighbour list by distance and
-// keeps the K nearest.  Here one warp owns one target: it streams the candidates inside the
-// target's current search radius H (the same culled cell stream as the density pass) and keeps
-// their squared distances in a per-warp buffer, cut back to its K nearest whenever it would
-// overflow.  With at least K candidates inside H the K-th smallest is selected with a warp radix
-// select (8-bit digits on the IEEE bit patterns, which order non-negative floats); h = sqrt of
-// it.  With fewer, H grows and the target returns in the next pass.
-// FP32: squared distances of the FP32 offsets, as in the FP32 density pairs.  FP64: formed
-// from the FP64 positions exactly as the FP64 pairs (and the oracle) form them.
-
-constexpr int kKnnWarps = 8;
-constexpr int kKnnThreads = 32 * kKnnWarps;
-constexpr int kKnnCap = 1024;  // buffered squared distances per warp (SPH_KNN_MAX_K = cap / 2)
-constexpr int kKnnLoads = 4;   // independent candidate loads per lane per stream round
-
-template <bool kF64>
-__host__ __device__ constexpr int knn_cap() { return kKnnCap; }
-template <bool kF64>
-__host__ __device__ constexpr int knn_buf_bytes() { return kKnnCap * (kF64 ? 8 : 4); }
-template <bool kF64>
-__host__ __device__ constexpr int knn_warp_bytes() { return knn_buf_bytes<kF64>() + 256 * 4 + 2 * kMaxCells * 4; }
-
-// K-th smallest (1-based) of the c keys; every round keeps the keys that agree with the digits
-// chosen so far and histograms their next digit.
-template <typename U>
-__device__ __forceinline__ U radix_select(const U *__restrict__ keys, int c, int K, int *hist)
-{
-    const int lane = lane_id();
-    U prefix = 0, mask = 0;
-    int kk = K;
-#pragma unroll 1
-    for (int shift = 8 * (int)sizeof(U) - 8; shift >= 0; shift -= 8) {
-        for (int b = lane; b < 256; b += 32) hist[b] = 0;
-        __syncwarp();
-        for (int i = lane; i < c; i += 32) {
-            const U v = keys[i];
-            if ((v & mask) == prefix) atomicAdd(&hist[(int)((v >> shift) & 0xff)], 1);
-        }
-        __syncwarp();
-        int loc[8];
-        int sum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            loc[q] = hist[8 * lane + q];
-            sum += loc[q];
-        }
-        const int incl = warp_inclusive_scan(sum);
-        const int excl = incl - sum;
-        const bool mine = excl < kk && kk <= incl;
-        int bin = 0, below = 0;
-        if (mine) {
-            int acc = excl;
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                if (bin == 0 && below == 0 && acc + loc[q] >= kk && acc < kk) {
-                    bin = 8 * lane + q;
-                    below = acc;
-                }
-                acc += loc[q];
-            }
-        }
-        const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
-        bin = __shfl_sync(kFull, bin, src);
-        below = __shfl_sync(kFull, below, src);
-        kk -= below;
-        prefix |= (U)bin << shift;
-        mask |= (U)0xff << shift;
-        __syncwarp();
-    }
-    return prefix;
-}
-
-template <bool kF64>
-__global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
-    k_knn(SolveArgs a, const int32_t *__restrict__ todo, int K)
-{
-    using T = typename std::conditional<kF64, double, float>::type;
-    using U = typename std::conditional<kF64, unsigned long long, unsigned>::type;
-    constexpr int cap = knn_cap<kF64>();
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wb = smem + (size_t)warp * knn_warp_bytes<kF64>();
-    T *buf = (T *)wb;
-    int *hist = (int *)(wb + knn_buf_bytes<kF64>());
-    int *cpre = hist + 256;
-    int *cbeg = cpre + kMaxCells;
-    const int n_todo = a.ds->pass_count;
-    const int pass = a.ds->pass;
-    int exceeded = 0;
-    unsigned long long tests = 0, listed = 0;
-
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&a.ds->item_head, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= n_todo) break;
-        const int p = todo[t];
-        const double H = a.h[p];
-        const uint4 P = a.pfix[p];
-        const int g = a.kl.seg_bits > 0 ? (int)(a.key[p] >> (3 * a.kl.lmax)) : 0;
-        const SegInfo &S = a.segs[g];
-        const float Hf = (float)H;
-        ItemGeom G3;
-        int rel[3];
-        // the box only needs to contain the ball of radius H, so the FP32 radius is enlarged
-        item_setup(S, a.kl, a.cell_div, true, P, Hf * (1.0f + 1.0f / 1048576.0f), G3, rel);
-        const float qf[3] = {(float)S.q[0], (float)S.q[1], (float)S.q[2]};
-        const float qm = fmaxf(qf[0], fmaxf(qf[1], qf[2]));
-        const float Rm = Hf * (1.0f + 1e-5f) + 8.0f * qm;
-        const float ball2 = Rm * Rm;
-        const int ncell = G3.nc[0] * G3.nc[1] * G3.nc[2];
-        if (ncell > kMaxCells) {  // cannot happen by construction; report, never overrun
-            if (lane == 0) atomicOr(&a.ds->status, 8);
-            continue;
-        }
-        long long rr[2];
-        {
-            const float cc[3] = {0.f, 0.f, 0.f};
-            item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, cc, ball2, qf, rr);
-        }
-        const float H2f = Hf * Hf;
-        const double H2 = __dmul_rn(H, H);
-        double4_32a ti = make_double4_32a(0, 0, 0, 0);
-        if (kF64) ti = a.pdbl[p];
-
-        int total;
-        {
-            const int b0 = (int)(rr[0] & 0xffffffffll), n0 = (int)(rr[0] >> 32) - b0;
-            const int b1 = (int)(rr[1] & 0xffffffffll), n1 = (int)(rr[1] >> 32) - b1;
-            const int i0 = warp_inclusive_scan(n0), i1 = warp_inclusive_scan(n1);
-            const int tot0 = __shfl_sync(kFull, i0, 31);
-            total = tot0 + __shfl_sync(kFull, i1, 31);
-            __syncwarp();
-            cpre[lane] = i0 - n0;
-            cbeg[lane] = b0;
-            cpre[lane + 32] = tot0 + i1 - n1;
-            cbeg[lane + 32] = b1;
-            __syncwarp();
-        }
-        int cc = 0, coff = cbeg[0], cnxt = cpre[1];
-        // The buffer holds candidates inside H.  When it would overflow it is cut to the
-        // entries at or below its K-th smallest value tau; from then on only candidates at or
-        // below tau enter (tau only falls, so every value below the final tau stays, and the
-        // K-th smallest of the buffer at the end is the K-th smallest inside H).
-        int seen = 0;  // candidates strictly inside H
-        int c = 0;     // entries in the buffer
-        bool cut = false, stuck = false;
-        T tau = 0;
-        for (int base = 0; base < total; base += 32 * kKnnLoads) {
-          // the round's loads are all issued before any is used
-          int jj[kKnnLoads];
-          uint4 PP[kKnnLoads];
-#pragma unroll
-          for (int u = 0; u < kKnnLoads; u++) {
-            const int f = base + 32 * u + lane;
-            if (f < total && cnxt <= f) {
-                int ci = cc;
-#pragma unroll
-                for (int step = kMaxCells / 2; step > 0; step >>= 1)
-                    if (ci + step < kMaxCells && cpre[ci + step] <= f) ci += step;
-                cc = ci;
-                coff = cbeg[ci] - cpre[ci];
-                cnxt = ci + 1 < kMaxCells ? cpre[ci + 1] : INT_MAX;
-            }
-            jj[u] = f < total ? f + coff : -1;
-            PP[u] = make_uint4(0, 0, 0, 0);
-            if (jj[u] >= 0) PP[u] = a.pfix[jj[u]];
-          }
-#pragma unroll
-          for (int u = 0; u < kKnnLoads; u++) {
-            const int j = jj[u];
-            bool in = false;
-            T r2 = 0;
-            if (j >= 0) {
-                // one target: its offsets are wrapped minimum images, and a candidate outside
-                // the query box also fails the radius test, so no box test is needed
-                const uint4 Pj = PP[u];
-                const int rj[3] = {(int32_t)(Pj.x - G3.X0[0]), (int32_t)(Pj.y - G3.X0[1]),
-                                   (int32_t)(Pj.z - G3.X0[2])};
-                {
-                    const float fx = (float)rj[0] * qf[0], fy = (float)rj[1] * qf[1],
-                                fz = (float)rj[2] * qf[2];
-                    const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-                    if (kF64) {
-                        if (r2f <= ball2) {
-                            const double4_32a cj = a.pdbl[j];
-                            double dx = __dsub_rn(cj.x, ti.x);
-                            double dy = __dsub_rn(cj.y, ti.y);
-                            double dz = __dsub_rn(cj.z, ti.z);
-                            if (S.periodic) {
-                                dx = min_image64(dx, S.box[0]);
-                                dy = min_image64(dy, S.box[1]);
-                                dz = min_image64(dz, S.box[2]);
-                            }
-                            const double d2 =
-                                __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                            r2 = (T)d2;
-                            in = d2 < H2;
-                        }
-                    } else {
-                        r2 = (T)r2f;
-                        in = r2f < H2f;
-                    }
-                }
-            }
-            seen += __popc(__ballot_sync(kFull, in));
-            bool keep = in && (!cut || r2 <= tau);
-            unsigned m = __ballot_sync(kFull, keep);
-            if (c + __popc(m) > cap && !stuck) {
-                const U kth = radix_select<U>((const U *)buf, c, K, hist);
-                memcpy(&tau, &kth, sizeof(T));
-                cut = true;
-                int nc = 0;
-                for (int i0 = 0; i0 < c; i0 += 32) {
-                    const int i = i0 + lane;
-                    T v = 0;
-                    bool kp = false;
-                    if (i < c) {
-                        v = buf[i];
-                        kp = v <= tau;
-                    }
-                    __syncwarp();  // the round's reads come before any of its writes
-                    const unsigned km = __ballot_sync(kFull, kp);
-                    if (kp) buf[nc + __popc(km & lanemask_lt())] = v;
-                    nc += __popc(km);
-                    __syncwarp();
-                }
-                c = nc;
-                // more than cap - 32 entries equal tau: no room can be made (handled below)
-                stuck = c + 32 > cap;
-                keep = in && r2 <= tau;
-                m = __ballot_sync(kFull, keep);
-            }
-            if (!stuck) {
-                if (keep) buf[c + __popc(m & lanemask_lt())] = r2;
-                c += __popc(m);
-            }
-          }
-        }
-        tests += (unsigned long long)total;
-        listed += (unsigned long long)seen;
-        __syncwarp();
-
-        int alive = 0;
-        if (seen >= K && !stuck) {
-            const U key = radix_select<U>((const U *)buf, c, K, hist);
-            T r2k;
-            memcpy(&r2k, &key, sizeof(T));
-            const double h = kF64 ? __dsqrt_rn((double)r2k) : sqrt((double)r2k);
-            if (S.periodic && h >= S.half_box) {
-                exceeded++;
-                if (lane == 0) a.e_h[p] = H;
-            } else if (lane == 0) {
-                a.e_h[p] = h;
-            }
-        } else {
-            // bracket: lo holds fewer than K candidates, hi a radius where the buffer could not
-            // be cut.  Growing, the count is taken to scale as H^3 and H aims at 2K candidates;
-            // with both sides known the bracket is halved geometrically (the count is monotone
-            // in H, so this ends even where density changes steeply)
-            double lo = a.hlo[p], hi = a.hhi[p];
-            if (seen < K) lo = H;
-            else hi = H;  // stuck: thousands of equal distances inside H
-            double hn;
-            if (lo > 0.0 && hi < HUGE_VAL) {
-                hn = sqrt(lo * hi);
-            } else if (seen < K) {
-                hn = H * fmin(fmax(cbrt(2.0 * K / (double)(seen > 0 ? seen : 1)), 1.05), 4.0);
-            } else {
-                hn = H * 0.5;
-            }
-            if (lane == 0) {
-                a.hlo[p] = lo;
-                a.hhi[p] = hi;
-            }
-            if (S.periodic && hn >= S.half_box) {
-                if (H >= S.half_box * 0.9999) {
-                    exceeded++;  // fewer than K particles within the largest legal radius
-                    hn = H;
-                } else {
-                    hn = S.half_box * 0.99999;
-                    alive = 1;
-                }
-            } else {
-                alive = 1;
-            }
-            if (lane == 0) {
-                a.h[p] = hn;
-                a.h32[p] = (float)hn;
-                a.e_h[p] = hn;
-            }
-        }
-        if (lane == 0) a.flags[t] = alive;
-    }
-    if (lane == 0) {
-        if (exceeded) atomicAdd(&a.ds->exceeded, exceeded);
-        if (tests) atomicAdd(&a.ds->pair_tests, tests);
-        if (listed) {
-            atomicAdd(&a.ds->pair_evals, listed);
-            if (pass < kMaxPasses) atomicAdd(&a.ds->pairs_per_pass[pass], listed);
-        }
-    }
-}
-
 }  // namespace
 
 template <int kMode, int kKern>
@@ -1176,32 +687,5 @@ cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t
     return cudaGetLastError();
 }
 
-
-template <bool kF64>
-int knn_blocks_per_sm()
-{
-    const int bytes = kKnnWarps * knn_warp_bytes<kF64>();
-    cudaFuncSetAttribute(k_knn<kF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_knn<kF64>, kKnnThreads, bytes);
-    return b > 0 ? b : 1;
-}
-
-int knn_capacity(int precision) { return precision == 0 ? knn_cap<true>() : knn_cap<false>(); }
-
-cudaError_t launch_knn(const SolveArgs &a, const int32_t *todo, int k, cudaStream_t st)
-{
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (a.precision == 0)
-        k_knn<true><<<sms * knn_blocks_per_sm<true>(), kKnnThreads, kKnnWarps * knn_warp_bytes<true>(), st>>>(
-            a, todo, k);
-    else
-        k_knn<false><<<sms * knn_blocks_per_sm<false>(), kKnnThreads, kKnnWarps * knn_warp_bytes<false>(),
-                       st>>>(a, todo, k);
-    if (a.launches) *a.launches += 1;
-    return cudaGetLastError();
-}
 
 }  // namespace sph
