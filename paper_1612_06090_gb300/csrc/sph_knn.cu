@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
             total = tot0 + __shfl_sync(kFull, i1, 31);
             __syncwarp();
             cpre[lane] = i0 - n0;
-            cbeg[lane] = b0;
+            cbeg[lane] = b0 - (i0 - n0);  // index offset: particle = position + offset
             cpre[lane + 32] = tot0 + i1 - n1;
-            cbeg[lane + 32] = b1;
+            cbeg[lane + 32] = b1 - (tot0 + i1 - n1);
             __syncwarp();
         }
         int cc = 0, coff = cbeg[0], cnxt = cpre[1];
@@ -170,12 +170,11 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
           for (int u = 0; u < kKnnLoads; u++) {
             const int f = base + 32 * u + lane;
             if (f < total && cnxt <= f) {
+                // positions only grow: step to the cell holding f (empty cells are passed over)
                 int ci = cc;
-#pragma unroll
-                for (int step = kMaxCells / 2; step > 0; step >>= 1)
-                    if (ci + step < kMaxCells && cpre[ci + step] <= f) ci += step;
+                while (ci + 1 < kMaxCells && cpre[ci + 1] <= f) ci++;
                 cc = ci;
-                coff = cbeg[ci] - cpre[ci];
+                coff = cbeg[ci];
                 cnxt = ci + 1 < kMaxCells ? cpre[ci + 1] : INT_MAX;
             }
             jj[u] = f < total ? f + coff : -1;
