@@ -18,8 +18,11 @@ namespace {
 
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
-constexpr int kSubTile = 2048;        // keys per warp in the radix passes
 constexpr int kSortThreads = 256;     // 8 warps per block
+constexpr int kTileKeys = 4096;       // keys per block tile in the radix passes
+constexpr int kKeysPerThread = kTileKeys / kSortThreads;
+constexpr int kWarpKeys = kTileKeys / (kSortThreads / 32);  // contiguous keys ranked by one warp
+static_assert(kSortThreads == kRadixBins, "one thread per digit in the tile offsets");
 
 // Periodic fixed point: nearest multiple of q = L / 2^32, wrapped (L itself maps to 0).
 __device__ __forceinline__ uint32_t fix_periodic(double x, double inv_q)
@@ -102,66 +105,117 @@ __global__ void k_keys_open(int64_t n, const double *__restrict__ pos,
 }
 
 // ---------------------------------------------------------------------------------------
-// LSD radix sort, 8-bit digits.  Each warp owns a sub-tile of kSubTile keys; the digit
-// histogram is laid out digit-major over sub-tiles so that one exclusive scan gives every
-// (digit, sub-tile) its output offset; the scatter ranks equal digits within a round of 32
-// keys with __match_any_sync, which keeps the sort stable.
+// LSD radix sort, 8-bit digits, over tiles of kTileKeys keys (one block per tile).
+// The digit counts of every tile are laid out digit-major, so one exclusive scan gives each
+// (digit, tile) its first output position.  The scatter ranks the tile stably: warp w owns
+// keys [w*kWarpKeys, (w+1)*kWarpKeys) of the tile and ranks equal digits round by round with
+// __match_any_sync; per-warp digit counts then give every key its place in the tile ordered
+// by digit.  The tile is reordered in shared memory and written out so that the keys of one
+// digit go to consecutive addresses (whole sectors instead of scattered 8-byte writes).
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t *__restrict__ key,
                                                              int64_t n, int shift,
                                                              int32_t *__restrict__ hist,
-                                                             int64_t n_sub)
+                                                             int64_t n_tiles)
 {
-    __shared__ int counts[kSortThreads / 32][kRadixBins];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *c = counts[warp];
-    const int64_t warps_total = (int64_t)gridDim.x * (kSortThreads / 32);
-    for (int64_t s = blockIdx.x * (int64_t)(kSortThreads / 32) + warp; s < n_sub; s += warps_total) {
-        for (int d = lane; d < kRadixBins; d += 32) c[d] = 0;
-        __syncwarp();
-        const int64_t base = s * kSubTile;
-        const int64_t end = base + kSubTile < n ? base + kSubTile : n;
-        for (int64_t i = base + lane; i < end; i += 32) {
-            int d = (int)((key[i] >> shift) & (kRadixBins - 1));
-            atomicAdd(&c[d], 1);
+    __shared__ int cnt[kRadixBins];
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = t * kTileKeys;
+#pragma unroll 4
+        for (int k = 0; k < kKeysPerThread; k++) {
+            const int64_t i = base + k * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&cnt[(int)((key[i] >> shift) & (kRadixBins - 1))], 1);
         }
-        __syncwarp();
-        for (int d = lane; d < kRadixBins; d += 32) hist[(int64_t)d * n_sub + s] = c[d];
-        __syncwarp();
+        __syncthreads();
+        hist[(int64_t)threadIdx.x * n_tiles + t] = cnt[threadIdx.x];
+        __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+struct ScatterSmem {
+    uint64_t keys[kTileKeys];                 // the tile in digit order
+    int32_t idx[kTileKeys];
+    int wcnt[kSortThreads / 32][kRadixBins];  // per-warp digit counts, then their prefix over warps
+    int dstart[kRadixBins];                   // first position of each digit in the tile
+    int goff[kRadixBins];                     // first output position of each digit of the tile
+    int wsum[kSortThreads / 32];
+};
+
+__global__ void __launch_bounds__(kSortThreads, 2) k_radix_scatter(
     const uint64_t *__restrict__ key_in, const int32_t *__restrict__ idx_in,
     uint64_t *__restrict__ key_out, int32_t *__restrict__ idx_out, int64_t n, int shift,
-    const int32_t *__restrict__ offs, int64_t n_sub)
+    const int32_t *__restrict__ offs, int64_t n_tiles)
 {
-    __shared__ int cursor[kSortThreads / 32][kRadixBins];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *c = cursor[warp];
-    const int64_t warps_total = (int64_t)gridDim.x * (kSortThreads / 32);
-    for (int64_t s = blockIdx.x * (int64_t)(kSortThreads / 32) + warp; s < n_sub; s += warps_total) {
-        for (int d = lane; d < kRadixBins; d += 32) c[d] = offs[(int64_t)d * n_sub + s];
-        __syncwarp();
-        const int64_t base = s * kSubTile;
-        const int64_t end = base + kSubTile < n ? base + kSubTile : n;
-        for (int64_t r = base; r < end; r += 32) {
-            const int64_t i = r + lane;
-            const bool valid = i < end;
-            uint64_t k = valid ? key_in[i] : 0;
-            int32_t v = valid ? idx_in[i] : 0;
-            int d = valid ? (int)((k >> shift) & (kRadixBins - 1)) : kRadixBins + lane;
-            unsigned peers = __match_any_sync(kFull, d);
-            int rank = __popc(peers & lanemask_lt());
-            if (valid) {
-                int p = c[d] + rank;
-                key_out[p] = k;
-                idx_out[p] = v;
-            }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t base = t * kTileKeys;
+        const int64_t wbase = base + (int64_t)warp * kWarpKeys;
+        for (int e = tid; e < (kSortThreads / 32) * kRadixBins; e += kSortThreads) (&S.wcnt[0][0])[e] = 0;
+        uint64_t kv[kKeysPerThread];
+        int32_t iv[kKeysPerThread];
+        int pos[kKeysPerThread];
+#pragma unroll
+        for (int k = 0; k < kKeysPerThread; k++) {
+            const int64_t i = wbase + k * 32 + lane;
+            kv[k] = i < n ? key_in[i] : 0ull;
+            iv[k] = i < n ? idx_in[i] : 0;
+        }
+        __syncthreads();
+        // stable rank inside the warp's keys, round by round
+#pragma unroll
+        for (int k = 0; k < kKeysPerThread; k++) {
+            const bool valid = wbase + k * 32 + lane < n;
+            const int d = valid ? (int)((kv[k] >> shift) & (kRadixBins - 1)) : kRadixBins + lane;
+            const unsigned peers = __match_any_sync(kFull, d);
+            const int rank = __popc(peers & lanemask_lt());
+            pos[k] = valid ? S.wcnt[warp][d] + rank : 0;
             __syncwarp();
-            if (valid && rank == 0) c[d] += __popc(peers);
+            if (valid && rank == 0) S.wcnt[warp][d] += __popc(peers);
             __syncwarp();
         }
+        __syncthreads();
+        {
+            // thread = digit: prefix over warps, then the digit starts by a block scan
+            const int d = tid;
+            int tot = 0;
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; w++) {
+                const int c = S.wcnt[w][d];
+                S.wcnt[w][d] = tot;
+                tot += c;
+            }
+            const int incl = warp_inclusive_scan(tot);
+            if (lane == 31) S.wsum[warp] = incl;
+            S.goff[d] = offs[(int64_t)d * n_tiles + t];
+            __syncthreads();
+            int before = 0;
+            for (int w = 0; w < warp; w++) before += S.wsum[w];
+            S.dstart[d] = before + incl - tot;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKeysPerThread; k++) {
+            if (wbase + k * 32 + lane < n) {
+                const int d = (int)((kv[k] >> shift) & (kRadixBins - 1));
+                const int p = S.dstart[d] + S.wcnt[warp][d] + pos[k];
+                S.keys[p] = kv[k];
+                S.idx[p] = iv[k];
+            }
+        }
+        __syncthreads();
+        const int valid_n = (int)(n - base < kTileKeys ? n - base : kTileKeys);
+        for (int p = tid; p < valid_n; p += kSortThreads) {
+            const uint64_t kk = S.keys[p];
+            const int d = (int)((kk >> shift) & (kRadixBins - 1));
+            const int64_t g = (int64_t)S.goff[d] + (p - S.dstart[d]);
+            key_out[g] = kk;
+            idx_out[g] = S.idx[p];
+        }
+        __syncthreads();
     }
 }
 
@@ -322,7 +376,7 @@ int blocks_for(int64_t n, int threads, int cap)
 
 }  // namespace
 
-int64_t radix_hist_size(int64_t n_max) { return (int64_t)kRadixBins * ((n_max + kSubTile - 1) / kSubTile + 1); }
+int64_t radix_hist_size(int64_t n_max) { return (int64_t)kRadixBins * ((n_max + kTileKeys - 1) / kTileKeys + 1); }
 
 cudaError_t launch_keys_periodic(const SortArgs &a, int64_t n, const double *pos, const double *mass,
                                  const SegInfo &seg, const double box[3], cudaStream_t st)
@@ -362,18 +416,19 @@ cudaError_t launch_keys_open(const SortArgs &a, int64_t n, const double *pos, co
 // index holding the result in *which.
 cudaError_t launch_radix_sort(const SortArgs &a, int64_t n, int *which, cudaStream_t st)
 {
-    const int64_t n_sub = (n + kSubTile - 1) / kSubTile;
-    const int warps_per_block = kSortThreads / 32;
-    int grid = blocks_for(n_sub, warps_per_block, a.grid_cap);
+    const int64_t n_tiles = (n + kTileKeys - 1) / kTileKeys;
+    const int grid = blocks_for(n_tiles, 1, a.grid_cap);
+    const int smem = (int)sizeof(ScatterSmem);
+    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int cur = 0;
     for (int shift = 0; shift < a.kl.key_bits; shift += kRadixBits) {
-        k_radix_hist<<<grid, kSortThreads, 0, st>>>(a.key[cur], n, shift, a.hist, n_sub);
+        k_radix_hist<<<grid, kSortThreads, 0, st>>>(a.key[cur], n, shift, a.hist, n_tiles);
         if (a.launches) *a.launches += 1;
-        cudaError_t e = scan_exclusive(a.hist, a.hist_off, (int64_t)kRadixBins * n_sub, nullptr, nullptr,
+        cudaError_t e = scan_exclusive(a.hist, a.hist_off, (int64_t)kRadixBins * n_tiles, nullptr, nullptr,
                                        a.scan_aux, a.grid_cap, st, a.launches);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<grid, kSortThreads, 0, st>>>(a.key[cur], a.idx[cur], a.key[1 - cur],
-                                                        a.idx[1 - cur], n, shift, a.hist_off, n_sub);
+        k_radix_scatter<<<grid, kSortThreads, smem, st>>>(a.key[cur], a.idx[cur], a.key[1 - cur],
+                                                          a.idx[1 - cur], n, shift, a.hist_off, n_tiles);
         if (a.launches) *a.launches += 1;
         cur = 1 - cur;
     }
