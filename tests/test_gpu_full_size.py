@@ -6,6 +6,8 @@ positions and masses) by brute-force neighbour search, which needs no per-level 
 tens of millions of particles.  Batched groups are independent, so a sample of whole groups
 (always including the largest) is solved by the oracle and compared group by group.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -51,8 +53,13 @@ def _sample_check(wl, g, n_samples, seed, precision, h0=None):
                        max_mismatch_frac=0.05, count_exact=fp64, mode="brute"), o
 
 
+@functools.lru_cache(maxsize=1)
+def _c3():
+    return inputs.make("c3")
+
+
 def test_config3_lognormal_16M_sampled():
-    wl = inputs.make("c3")
+    wl = _c3()
     g = _solve(wl, B.SPH_PREC_FP32_KAHAN)
     assert g["status"] == B.SPH_OK
     _sample_check(wl, g, 96, 303, B.SPH_PREC_FP32_KAHAN)
@@ -101,3 +108,24 @@ def test_config4_batched_groups_sampled(precision):
         check_solve(wl.pos[:, s0:e0], wl.mass[s0:e0], (0, 0, 0), False, 32.0, 1.0, gs, o,
                     np.arange(e0 - s0), rtol=1e-5, delta=1e-5 * 32, max_mismatch_frac=0.05,
                     count_exact=False)
+
+
+def test_config3_lognormal_16M_knn_sampled():
+    # the k-nearest-neighbour h at the paper's K = 295 on the 16.7M log-normal field (densities
+    # spanning orders of magnitude), FP32 with estimated start radii, against the oracle's full
+    # sort of every distance for sampled targets
+    wl = _c3()
+    s = B.Solver(wl.n, precision=B.SPH_PREC_FP32_KAHAN, box=wl.box)
+    s.sort(T(wl.pos), T(wl.mass))
+    r = s.knn(295, torch.zeros(wl.n, dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    g = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    s.close()
+    assert g["status"] == B.SPH_OK
+    rng = np.random.default_rng(295)
+    tg = np.sort(rng.choice(wl.n, size=48, replace=False))
+    o = oracle.knn(wl.pos, wl.mass, 295, targets=tg, mode="brute")
+    assert np.max(rel_err(g["h"][tg], o["h"])) <= 2e-6
+    assert np.max(rel_err(g["rho"][tg], o["rho"])) <= 1e-5
+    e = oracle.evaluate(wl.pos, wl.mass, g["h"][tg], targets=tg, near_rel=2e-6, mode="brute")
+    assert np.all(np.abs(g["count"][tg].astype(np.int64) - e["count"]) <= e["near"])
