@@ -804,10 +804,9 @@ sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *r
     if (s != SPH_OK) return s;
     const DevState knn = *ctx->ds_host;
     if (knn.status) return device_status_error(ctx, knn.status);
-    // one density evaluation of every particle at its selected h
+    // the density of particles without a selection, at their last radius
     a.dens_ev[0] = a.dens_ev[1] = nullptr;
     CU(ctx, launch_knn_finish(a, st), "kNN finish");
-    CU(ctx, launch_pass(a, 0, false, st), "density pass");
     CU(ctx, launch_scatter(a, h_inout_dev, rho_out_dev, count_out_dev, nw_out_dev, nullptr, st), "scatter");
     CU(ctx, cudaEventRecord(ctx->ev[3], st), "event");
     s = read_state(ctx);

@@ -26,13 +26,13 @@ namespace {
 
 constexpr int kKnnWarps = 8;
 constexpr int kKnnThreads = 32 * kKnnWarps;
-constexpr int kKnnCap = 1024;  // buffered squared distances per warp (SPH_KNN_MAX_K = cap / 2)
+constexpr int kKnnCap = 768;   // buffered candidates per warp (>= SPH_KNN_MAX_K + 256)
 constexpr int kKnnLoads = 4;   // independent candidate loads per lane per stream round
 
 template <bool kF64>
 __host__ __device__ constexpr int knn_cap() { return kKnnCap; }
 template <bool kF64>
-__host__ __device__ constexpr int knn_buf_bytes() { return kKnnCap * (kF64 ? 8 : 4); }
+__host__ __device__ constexpr int knn_buf_bytes() { return kKnnCap * (kF64 ? 8 + 4 : 4 + 4); }
 template <bool kF64>
 __host__ __device__ constexpr int knn_warp_bytes() { return knn_buf_bytes<kF64>() + 256 * 4 + 2 * kMaxCells * 4; }
 
@@ -86,6 +86,91 @@ __device__ __forceinline__ U radix_select(const U *__restrict__ keys, int c, int
     return prefix;
 }
 
+// rho, N_w and the count at h over the buffered candidates (the target's own entry included),
+// in the precision of the pass.  FP64: the oracle's pair terms; FP32: single-precision terms and
+// sums (at most K - 1 + ties terms per target).
+template <bool kF64, typename T>
+__device__ void knn_density(const SolveArgs &a, int p, double h, const T *__restrict__ buf,
+                            const int *__restrict__ bidx, int c)
+{
+    const int lane = lane_id();
+    const bool c6 = a.kernel != 0;
+    if (kF64) {
+        const double h2 = __dmul_rn(h, h);
+        double smw = 0.0, sw = 0.0;
+        int cnt = 0;
+        for (int i = lane; i < c; i += 32) {
+            const double r2 = (double)buf[i];
+            if (r2 < h2) {
+                const double q = __ddiv_rn(__dsqrt_rn(r2), h);
+                double w;
+                if (c6) {
+                    const double u = __dsub_rn(1.0, q), u2 = __dmul_rn(u, u), u4 = __dmul_rn(u2, u2);
+                    const double poly = __dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(8.0, q)),
+                                                            __dmul_rn(25.0, __dmul_rn(q, q))),
+                                                  __dmul_rn(32.0, __dmul_rn(__dmul_rn(q, q), q)));
+                    w = __dmul_rn(__dmul_rn(u4, u4), poly);
+                } else if (q <= 0.5) {
+                    w = __dadd_rn(1.0, __dmul_rn(__dmul_rn(q, q), __dsub_rn(__dmul_rn(6.0, q), 6.0)));
+                } else {
+                    const double u = __dsub_rn(1.0, q);
+                    w = __dmul_rn(2.0, __dmul_rn(__dmul_rn(u, u), u));
+                }
+                smw = __dadd_rn(smw, __dmul_rn(a.pdbl[bidx[i]].w, w));
+                sw = __dadd_rn(sw, w);
+                cnt++;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            smw += __shfl_xor_sync(kFull, smw, o);
+            sw += __shfl_xor_sync(kFull, sw, o);
+        }
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (lane == 0) {
+            const double kPi = 3.14159265358979323846;
+            a.e_h[p] = h;
+            a.e_rho[p] = smw * (c6 ? 1365.0 / (64.0 * kPi * h * h * h) : 8.0 / (kPi * h * h * h));
+            a.e_nw[p] = (c6 ? 1365.0 / 48.0 : 32.0 / 3.0) * sw;
+            a.e_cnt[p] = cnt;
+        }
+    } else {
+        const float hf = (float)h, h2 = hf * hf, hinv = 1.0f / hf;
+        float smw = 0.f, sw = 0.f;
+        int cnt = 0;
+        for (int i = lane; i < c; i += 32) {
+            const float r2 = (float)buf[i];
+            if (r2 < h2) {
+                const float q = sqrtf(r2) * hinv;
+                float w;
+                if (c6) {
+                    const float u = fmaxf(1.f - q, 0.f), u2 = u * u, u4 = u2 * u2;
+                    w = u4 * u4 * fmaf(q, fmaf(q, fmaf(q, 32.f, 25.f), 8.f), 1.f);
+                } else if (q <= 0.5f) {
+                    w = fmaf(q * q, fmaf(6.f, q, -6.f), 1.f);
+                } else {
+                    const float u = fmaxf(1.f - q, 0.f);
+                    w = 2.f * u * u * u;
+                }
+                smw = fmaf(__uint_as_float(a.pfix[bidx[i]].w), w, smw);
+                sw += w;
+                cnt++;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            smw += __shfl_xor_sync(kFull, smw, o);
+            sw += __shfl_xor_sync(kFull, sw, o);
+        }
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (lane == 0) {
+            const float kPif = 3.14159265f;
+            a.e_h[p] = h;
+            a.e_rho32[p] = smw * (c6 ? 1365.0f / (64.0f * kPif) : 8.0f / kPif) * (hinv * hinv * hinv);
+            a.e_nw32[p] = (c6 ? 1365.0f / 48.0f : 32.0f / 3.0f) * sw;
+            a.e_cnt[p] = cnt;
+        }
+    }
+}
+
 template <bool kF64>
 __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
     k_knn(SolveArgs a, const int32_t *__restrict__ todo, int K)
@@ -96,7 +181,8 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = smem + (size_t)warp * knn_warp_bytes<kF64>();
-    T *buf = (T *)wb;
+    T *buf = (T *)wb;                          // squared distances
+    int *bidx = (int *)(wb + kKnnCap * sizeof(T));  // their candidates' sorted positions
     int *hist = (int *)(wb + knn_buf_bytes<kF64>());
     int *cpre = hist + 256;
     int *cbeg = cpre + kMaxCells;
@@ -229,14 +315,19 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
                 for (int i0 = 0; i0 < c; i0 += 32) {
                     const int i = i0 + lane;
                     T v = 0;
+                    int vj = 0;
                     bool kp = false;
                     if (i < c) {
                         v = buf[i];
+                        vj = bidx[i];
                         kp = v <= tau;
                     }
                     __syncwarp();  // the round's reads come before any of its writes
                     const unsigned km = __ballot_sync(kFull, kp);
-                    if (kp) buf[nc + __popc(km & lanemask_lt())] = v;
+                    if (kp) {
+                        buf[nc + __popc(km & lanemask_lt())] = v;
+                        bidx[nc + __popc(km & lanemask_lt())] = vj;
+                    }
                     nc += __popc(km);
                     __syncwarp();
                 }
@@ -247,7 +338,11 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
                 m = __ballot_sync(kFull, keep);
             }
             if (!stuck) {
-                if (keep) buf[c + __popc(m & lanemask_lt())] = r2;
+                if (keep) {
+                    const int slot = c + __popc(m & lanemask_lt());
+                    buf[slot] = r2;
+                    bidx[slot] = j;
+                }
                 c += __popc(m);
             }
           }
@@ -265,8 +360,10 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
             if (S.periodic && h >= S.half_box) {
                 exceeded++;
                 if (lane == 0) a.e_h[p] = H;
-            } else if (lane == 0) {
-                a.e_h[p] = h;
+            } else {
+                // Eq. 1 at h from the buffer: every particle with r < h is in it (all entries
+                // at or below tau >= r_K^2 were kept)
+                knn_density<kF64>(a, p, h, buf, bidx, c);
             }
         } else {
             // bracket: lo holds fewer than K candidates, hi a radius where the buffer could not

@@ -76,6 +76,7 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
         a.hlo[p] = 0.0;
         a.hhi[p] = HUGE_VAL;
         a.e_h[p] = hv;
+        a.e_cnt[p] = -1;  // no selection yet
         a.todo[0][p] = (int32_t)p;
     }
     if (bad) atomicOr(&a.ds->status, bad);
@@ -122,6 +123,7 @@ __global__ void k_knn_init(SolveArgs a, const double *__restrict__ h_in, int max
         a.hlo[p] = 0.0;
         a.hhi[p] = HUGE_VAL;
         a.e_h[p] = hv;
+        a.e_cnt[p] = -1;  // no selection yet
         a.todo[0][p] = (int32_t)p;
     }
     if (bad) atomicOr(&a.ds->status, bad);
@@ -256,8 +258,9 @@ __global__ void k_scatter(SolveArgs a, double *__restrict__ h_out, double *__res
 }
 
 
-// After the kNN passes: every particle is evaluated once at its selected h (the last search
-// radius for one that did not finish), as a single pass over all particles.
+// After the kNN passes: a selected particle already has its density (summed from the
+// selection buffer); one that did not finish (pass or box limit) is evaluated at its last
+// search radius by one density pass over just those particles.
 __global__ void k_knn_finish(SolveArgs a)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n;
@@ -265,10 +268,9 @@ __global__ void k_knn_finish(SolveArgs a)
         const double h = a.e_h[p];
         a.h[p] = h;
         a.h32[p] = (float)h;
-        a.todo[0][p] = (int32_t)p;
+        a.flags[p] = a.e_cnt[p] < 0 ? 1 : 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ds->todo_count = (int32_t)a.n;
         a.ds->pass = 0;
         a.ds->max_iter = 1;
         a.ds->pair_evals = 0ull;
@@ -362,7 +364,11 @@ cudaError_t launch_knn_finish(const SolveArgs &a, cudaStream_t st)
 {
     k_knn_finish<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a);
     if (a.launches) *a.launches += 1;
-    return cudaGetLastError();
+    // the particles without a selection become the todo list of one density pass
+    cudaError_t e = compact_i32(a.flags, nullptr, a.todo[0], nullptr, a.n, nullptr, &a.ds->todo_count,
+                                a.scan_aux, a.grid_cap, st, a.launches);
+    if (e != cudaSuccess) return e;
+    return launch_pass(a, 0, false, st);
 }
 
 }  // namespace sph
