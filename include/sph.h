@@ -166,7 +166,7 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
  * h_inout_dev (n doubles, caller order): a starting search radius on entry (below min(box)/2;
  * it steers the passes, not the result), or <= 0 to have one estimated from the local cell
  * density; h_i on exit.  Each pass streams a target's candidates inside its radius through
- * a per-warp buffer of 768 squared distances that is cut back to its
+ * a per-warp buffer of 896 squared distances that is cut back to its
  * K nearest whenever it would overflow; with at least K inside the radius the K-th is
  * selected (radix select), otherwise the radius grows (count ~ radius^3) and the target
  * returns in the next pass, for at most max_iter passes.

@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kKnnWarps = 8;
 constexpr int kKnnThreads = 32 * kKnnWarps;
-constexpr int kKnnCap = 768;   // buffered candidates per warp (>= SPH_KNN_MAX_K + 256)
+constexpr int kKnnCap = 896;   // buffered candidates per warp (>= SPH_KNN_MAX_K + 256)
 constexpr int kKnnLoads = 4;   // independent candidate loads per lane per stream round
 
 template <bool kF64>

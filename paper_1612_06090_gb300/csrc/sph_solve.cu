@@ -85,7 +85,7 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
 
 // Starting search radii of the kNN passes.  A caller radius <= 0 is replaced by an estimate:
 // the particle's cell at the dense-table level, widened to coarser levels until it holds 32
-// particles, gives a local number density, and the radius is the one whose ball would hold 1.5K
+// particles, gives a local number density, and the radius is the one whose ball would hold 1.25K
 // particles at that density (capped below half the periodic box).  The radius only steers the
 // passes; the selected h does not depend on it.
 __global__ void k_knn_init(SolveArgs a, const double *__restrict__ h_in, int max_iter, int K)
@@ -114,7 +114,7 @@ __global__ void k_knn_init(SolveArgs a, const double *__restrict__ h_in, int max
             double vol = 1.0;
             for (int d = 0; d < 3; d++) vol *= ldexp(S.q[d], a.kl.coord_bits - l);
             const double dens = (double)(cnt > 0 ? cnt : 1) / vol;
-            hv = cbrt(3.0 * (1.5 * K) / (4.0 * 3.14159265358979323846 * dens));
+            hv = cbrt(3.0 * (1.25 * K) / (4.0 * 3.14159265358979323846 * dens));
             if (S.periodic) hv = fmin(hv, 0.999 * S.half_box);
         }
         if (!(hv > 0.0 && hv <= DBL_MAX) || (S.periodic && hv >= S.half_box)) bad |= kBadH;
