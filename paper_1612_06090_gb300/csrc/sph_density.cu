@@ -1,21 +1,23 @@
 // sph_density.cu -- the density pass: neighbour search + kernel sums for every target on
-// the todo list (Eq. 1 with the M4 kernel; the density loop of Listing 1).
+// the todo list (Eq. 1 with the M4 or Wendland C6 kernel; the density loop of Listing 1).
 //
 // Work decomposition.  The todo list (sorted positions of unconverged particles, in Morton
-// order) is cut into work items of up to 32 consecutive targets that share one octree cell
-// at their grouping level.  A persistent grid of warps pops items from a device counter
-// (the dynamic scheduling of Listing 3, without a lock).  Per item, the warp:
+// order) is cut into work items of up to 32 consecutive targets that share an octree cell
+// (sph_solve.cu).  A persistent grid of warps pops items from a device counter (the dynamic
+// scheduling of Listing 3, without a lock).  Per item, the warp:
 //   1. builds the item's query box Q = bounding box of the targets grown by h_max, in
-//      32-bit fixed point relative to the first target;
-//   2. picks the octree level whose cells are at least |Q|/3, so at most 4 x 4 x 4 cells
-//      meet Q, and looks each cell's particle range up (dense table at or above the
-//      table level, binary search on the sorted keys below it);
-//   3. streams those ranges with coalesced 16-byte loads, keeps the particles inside Q
-//      (ballot compaction) and stages them in shared memory as FP32 offsets from the
-//      first target (formed exactly in integer arithmetic, then rounded once);
-//   4. runs the pair loop with one target per lane over the staged candidates.
-// FP32 path: r < h test, kernel weights and partial sums in FP32, every 32 candidates
-// the partial sums enter compensated (Kahan) accumulators; the totals go to FP64.
+//      32-bit fixed point relative to the first target, and a ball around the targets' box
+//      centre that every in-h candidate lies in (sph_items.cuh);
+//   2. picks the octree level whose cells are at least |Q|/cell_div, skips the cells that
+//      lie outside the ball, and looks up each remaining cell's particle range (dense table
+//      at or above the table level, binary search on the sorted keys below it);
+//   3. streams all those cells as one list with coalesced 16-byte loads, keeps the particles
+//      inside Q and the ball (ballot compaction) and stages them in shared memory as FP32
+//      offsets from the first target (formed exactly in integer arithmetic, rounded once);
+//   4. runs the pair loop: lanes are (target, slice) pairs over the staged candidates.
+// FP32 path: each lane tests two candidates at a time with two-wide FP32 instructions and
+// evaluates the kernel under the r < h test; partial sums enter compensated (Kahan)
+// accumulators every 32 steps.
 // FP64 path: the staged FP32 offsets only pre-filter with a widened radius; every pair that
 // passes is recomputed from the FP64 positions exactly as the FP64 reference formulae are
 // written (IEEE roundings, no contraction), so neighbour sets and per-pair terms are the
@@ -579,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
 
         // combine the slices of each target
         int count = kF64 ? A64.count : A32.count;
-        if (kF64) {
+        if constexpr (kF64) {
             double smw = A64.s_mw, sw = A64.s_w, sdw = A64.s_dw;
             for (int o = Gp; o < 32; o <<= 1) {
                 smw += __shfl_xor_sync(kFull, smw, o);
