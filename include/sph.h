@@ -174,7 +174,8 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
  * Needs 2 <= k <= SPH_KNN_MAX_K and k <= n.  Returns OK; NOT_CONVERGED (passes ran out);
  * H_EXCEEDS_BOX (the K-th distance, or the radius that would hold K particles, reaches
  * min(box)/2); those particles report their last radius and the density there.  Errors:
- * INVALID_ARG, NOT_SORTED, UNSUPPORTED (after sph_batch_solve), DEVICE_STATUS, CUDA.
+ * INVALID_ARG, NOT_SORTED (no sph_sort since the context was created or since the last
+ * sph_batch_solve, which leaves groups, not one sorted set), DEVICE_STATUS, CUDA.
  * stats: passes/todo_per_pass/density_ms of the selection passes, pair_tests = candidates
  * streamed, pair_evals / pairs_per_pass = neighbour-list entries (squared distances inside
  * the search radius) built by the selection passes, unconverged, exceeded. */

@@ -172,3 +172,26 @@ def test_knn_full_size_c2_sampled():
     tg = np.sort(rng.choice(wl.n, size=96, replace=False))
     o = oracle.knn(wl.pos, wl.mass, 295, targets=tg, mode="brute")
     check_fp32(g, wl.pos, wl.mass, tg, 295, o)
+
+
+def test_knn_after_batch_solve_needs_a_sort_and_graph_contexts_work():
+    # kNN runs on the particles of sph_sort; a batched solve leaves groups, not one sorted set
+    wl = inputs.make("c4", n_groups=8, nmax=256)
+    s = B.Solver(wl.n, precision=FP32)
+    s.batch_solve(T(wl.offsets, torch.int64), T(wl.pos), T(wl.mass), T(wl.h0), T(wl.nngb), T(wl.tol))
+    h = torch.zeros(wl.n, dtype=torch.float64, device=DEV)
+    rho = torch.empty_like(h)
+    cnt = torch.empty(wl.n, dtype=torch.int32, device=DEV)
+    assert B.sph_knn_solve(s.ctx, 16, h.data_ptr(), rho.data_ptr(), cnt.data_ptr()) == B.SPH_ERR_NOT_SORTED
+    s.close()
+    # a context whose density solves run as CUDA graphs: the kNN passes run from the host and
+    # give the same answer
+    u = inputs.make("c1", n=4096)
+    ref = gpu_knn(u.pos, u.mass, 64, 0.0, FP64)
+    s = B.Solver(u.n, precision=FP64, use_graph=True)
+    s.sort(T(u.pos), T(u.mass))
+    r = s.knn(64, torch.zeros(u.n, dtype=torch.float64, device=DEV))
+    torch.cuda.synchronize()
+    s.close()
+    assert r["status"] == B.SPH_OK
+    np.testing.assert_array_equal(r["h"].cpu().numpy(), ref["h"])
