@@ -238,6 +238,8 @@ SolveArgs solve_args(sph_ctx *c)
     a.group_shift = c->tuning.group_shift;
     a.cell_div = c->tuning.cell_div;
     a.direct_pct = c->tuning.direct_pct;
+    a.free_first = (c->kl.seg_bits == 0 && c->params.precision != SPH_PREC_FP64 &&
+                    c->tuning.direct_pct == 0) ? 1 : 0;
     a.launches = &c->launches;
     return a;
 }
@@ -411,6 +413,7 @@ sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *coun
     }
     CU(c, cudaEventRecord(c->ev[2], st), "event");
     CU(c, cudaMemsetAsync(&c->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+    CU(c, cudaMemsetAsync(&c->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
     CU(c, launch_solve_init(a, h_inout, c->params.max_iter, st), "solve init");
     if (!graph) {
         s = read_state(c);
@@ -707,6 +710,7 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
             ctx->tuning = t;
             SolveArgs a = solve_args(ctx);
             CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+            CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
             CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
             CU(ctx, launch_solve_init(a, h_dev, ctx->params.max_iter, st), "init");
             int passes = 0;
@@ -749,6 +753,7 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
     cudaStream_t st = ctx->stream;
     SolveArgs a = solve_args(ctx);
     CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+    CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
     CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
     sph_status s = read_state(ctx);
     if (s != SPH_OK) return s;
@@ -779,6 +784,7 @@ sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *r
     cudaStream_t st = ctx->stream;
     const int launches0 = ctx->launches;
     SolveArgs a = solve_args(ctx);
+    a.free_first = 0;  // the density pass of leftover particles keeps the body under its test
     CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
     CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
     CU(ctx, launch_knn_init(a, h_inout_dev, ctx->params.max_iter, k, st), "init");

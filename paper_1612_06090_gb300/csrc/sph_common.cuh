@@ -61,6 +61,8 @@ struct DevState {
     int32_t loop_flag;         // 1 while another pass is needed (device-side loop)
     int32_t pass_count;        // entries this pass evaluates (0: the pass is skipped)
     int32_t sort_status;       // input errors found by the sort (kept across solves)
+    int32_t h_varies;          // some starting h differs from particle 0's (set by the solve init)
+    int32_t free_now;          // this pass runs the branch-free FP32 pair loop
     int32_t pad1;
     unsigned long long pair_evals;  // in-h pairs accumulated over the solve
     unsigned long long pair_tests;  // candidate-target distance tests (work done, not counted

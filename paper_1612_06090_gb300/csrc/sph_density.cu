@@ -264,9 +264,9 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
                                       const double4_32a *__restrict__ pdbl)
 {
     constexpr bool kF64 = kMode == 0;
-    constexpr bool kQueue = kMode != 2;
+    constexpr bool kQueue = kMode < 2;
     const int lane = lane_id();
-    if (kMode == 2) {
+    if (kMode >= 2) {
         // pad to a multiple of 2 S (an even number of steps per slice) with candidates that
         // are never within h
         const int pad = (cnt + (2 << L.sh) - 1) & ~((2 << L.sh) - 1);
@@ -288,9 +288,10 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
                 const float2 dz = __fadd2_rn(f2(B.x, B.y), ntz);
                 const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
                 const bool in0 = r2.x < L.h2, in1 = r2.y < L.h2;
-                // the pair body runs when either candidate is within h; a step in which no
-                // lane has one costs only the test
-                if (in0 || in1) {
+                // kMode 2: the pair body runs when either candidate is within h, so a step in
+                // which no lane has one costs only the test; kMode 3: branch-free, the
+                // unrolled bodies interleave (candidates outside h add exactly zero)
+                if (kMode == 3 || in0 || in1) {
                     pc = __fadd2_rn(pc, f2(in0 ? 1.f : 0.f, in1 ? 1.f : 0.f));
                     const float2 x = __fmul2_rn(r2, hinv2);
                     const float2 q = f2(fminf(sqrt_approx(x.x), 1.f), fminf(sqrt_approx(x.y), 1.f));
@@ -408,7 +409,7 @@ __host__ __device__ constexpr int warp_smem_bytes()
 }
 
 template <int kMode, int kKern>
-__global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
     k_density(SolveArgs a, const int32_t *__restrict__ todo)
 {
     constexpr bool kF64 = kMode == 0;
@@ -420,6 +421,9 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
     void *ring = wbase + kStageCap * 16 + (kF64 ? kStageCap * 4 : 0);
     int *cpre = (int *)(wbase + warp_cell_offset<kMode>());
     int *cbeg = cpre + kMaxCells;
+    // the branched (2) and branch-free (3) FP32 kernels are both launched when the pass may use
+    // either; the one the pass did not choose returns at once
+    if (kMode >= 2 && a.free_first && (a.ds->free_now != 0) != (kMode == 3)) return;
     const int n_items = a.ds->n_items;
     const int todo_count = a.ds->pass_count;
     const int pass = a.ds->pass;
@@ -560,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, kMode == 2 ? 3 : 2)
                 const unsigned m = __ballot_sync(kFull, in);
                 if (in) {
                     const int slot = cnt + __popc(m & lanemask_lt());
-                    if (kMode == 2) stage_pair_put((float *)stage, slot, L.sh, fx, fy, fz, __uint_as_float(Pj.w));
+                    if (kMode >= 2) stage_pair_put((float *)stage, slot, L.sh, fx, fy, fz, __uint_as_float(Pj.w));
                     else stage[slot] = make_float4(fx, fy, fz, __uint_as_float(Pj.w));
                     if (kF64) sidx[slot] = j;
                 }
@@ -666,7 +670,11 @@ int density_blocks_per_sm(int precision, int direct_pct)
     switch (mode_of(precision, direct_pct)) {
     case 0: blocks_per_sm<0, 1>(); return blocks_per_sm<0, 0>();
     case 1: blocks_per_sm<1, 1>(); return blocks_per_sm<1, 0>();
-    default: blocks_per_sm<2, 1>(); return blocks_per_sm<2, 0>();
+    default:
+        blocks_per_sm<3, 1>();
+        blocks_per_sm<3, 0>();
+        blocks_per_sm<2, 1>();
+        return blocks_per_sm<2, 0>();
     }
 }
 
@@ -683,7 +691,13 @@ cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t
     switch (mode_of(a.precision, a.direct_pct)) {
     case 0: launch_mode<0>(a, todo, st); break;
     case 1: launch_mode<1>(a, todo, st); break;
-    default: launch_mode<2>(a, todo, st); break;
+    default:
+        if (a.free_first) {
+            launch_mode<3>(a, todo, st);
+            if (a.launches) *a.launches += 1;
+        }
+        launch_mode<2>(a, todo, st);
+        break;
     }
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();

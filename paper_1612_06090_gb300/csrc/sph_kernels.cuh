@@ -73,6 +73,8 @@ struct SolveArgs {
                                // evaluates directly instead of queueing (101 = always queue)
     int precision;             // sph_precision
     int kernel;                // sph_kernel: 0 M4 cubic spline, 1 Wendland C6
+    int free_first;            // 1: the first pass of a solve from one common h runs the
+                               // branch-free FP32 pair loop (periodic FP32 direct solves)
     int *launches;
     cudaEvent_t dens_ev[2];    // optional events recorded around the density launch
 };

@@ -64,22 +64,24 @@ __device__ void reset_state(DevState *ds, int64_t n, int max_iter)
 __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int max_iter)
 {
     const int64_t n = a.n;
-    int bad = 0;
+    const double h_first = n > 0 ? h_in[0] : 0.0;
+    int bad = 0, varies = 0;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = a.idx[p];
         const double hv = h_in[i];
         const SegInfo &S = a.segs[seg_of(a.key[p], a.kl)];
         if (!(hv > 0.0 && hv <= DBL_MAX) || (S.periodic && hv >= S.half_box)) bad |= kBadH;
+        varies |= hv != h_first;
         a.h[p] = hv;
         a.h32[p] = (float)hv;
         a.hlo[p] = 0.0;
         a.hhi[p] = HUGE_VAL;
         a.e_h[p] = hv;
-        a.e_cnt[p] = -1;  // no selection yet
         a.todo[0][p] = (int32_t)p;
     }
     if (bad) atomicOr(&a.ds->status, bad);
+    if (varies) atomicOr(&a.ds->h_varies, 1);  // cleared by the host before this kernel
     if (blockIdx.x == 0 && threadIdx.x == 0) reset_state(a.ds, n, max_iter);
 }
 
@@ -132,12 +134,16 @@ __global__ void k_knn_init(SolveArgs a, const double *__restrict__ h_in, int max
 
 // A pass evaluates pass_count entries: the whole todo list while the loop runs, none once it
 // has converged or reached max_iter (so a pass queued after that is a no-op).
-__global__ void k_pass_begin(DevState *ds)
+// The branch-free FP32 pair loop runs in the first pass of a solve from one common h: every
+// target then has the same, usually generous, h, so nearly every step has a lane within h and
+// skipping the body never pays; later passes (and batches) keep the body under its test.
+__global__ void k_pass_begin(DevState *ds, int free_first)
 {
     ds->item_head = 0;
     ds->todo_next = 0;
     const bool run = ds->todo_count > 0 && ds->pass < ds->max_iter;
     ds->pass_count = run ? ds->todo_count : 0;
+    ds->free_now = free_first && ds->pass == 0 && !ds->h_varies;
     if (run && ds->pass < kMaxPasses) ds->todo_per_pass[ds->pass] = ds->todo_count;
 }
 
@@ -298,7 +304,7 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
 {
     const int32_t *todo = a.todo[cur];
     const int grid = blocks_for(a.n, a.grid_cap);
-    k_pass_begin<<<1, 1, 0, st>>>(a.ds);
+    k_pass_begin<<<1, 1, 0, st>>>(a.ds, a.free_first);
     k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
     if (a.launches) *a.launches += 2;
     // item starts = positions of the head flags
@@ -339,7 +345,7 @@ cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, i
 cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st)
 {
     const int32_t *todo = a.todo[cur];
-    k_pass_begin<<<1, 1, 0, st>>>(a.ds);
+    k_pass_begin<<<1, 1, 0, st>>>(a.ds, a.free_first);
     if (a.launches) *a.launches += 1;
     if (a.dens_ev[0]) cudaEventRecord(a.dens_ev[0], st);
     cudaError_t e = launch_knn(a, todo, k, st);
