@@ -340,7 +340,7 @@ def run_native(args):
     roof = {"bound": "alu", "kernel": "k_density<2> (FP32 pair loop)", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
             "traffic": profiled_traffic() if args.config == "c2" and not args.n else None,
-            "traffic_note": "mean DRAM bytes per density launch (ncu, profiles/density_fp32_c2_1M.md)",
+            "traffic_note": "mean DRAM bytes per density pass (ncu, profiles/density_fp32_c2_1M.md)",
             "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
             "flop_per_pair": FLOP_PER_PAIR, "pairs_per_step": pairs // max(1, len(st32)),
             "density_ms_per_step": dens_ms / max(1, len(st32)),
@@ -610,7 +610,7 @@ def run_knn(args):
 
 
 def profiled_traffic():
-    """Mean DRAM bytes per density launch from the committed ncu summary, valid only while the
+    """Mean DRAM bytes per density pass from the committed ncu summary, valid only while the
     kernel sources are the ones that summary was captured from (else None)."""
     import hashlib
     import re
@@ -622,7 +622,7 @@ def profiled_traffic():
         want = re.search(r"kernel_source_sha256_16: (\w+)", text).group(1)
         if hashlib.sha256(src).hexdigest()[:16] != want:
             return None
-        return int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+        return int(re.search(r"traffic_bytes_per_pass: (\d+)", text).group(1))
     except Exception:
         return None
 
