@@ -442,7 +442,7 @@ def run_native(args):
 
 
 def run_knn(args):
-    """k-nearest-neighbour smoothing lengths (Sec. IV-C): one step = sort + sph_knn_solve on
+    """k-nearest-neighbour smoothing lengths (Sec. IV-D): one step = sort + sph_knn_solve on
     the workload, h = distance to the K-th nearest particle and rho at that h."""
     import numpy as np
     import torch

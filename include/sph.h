@@ -155,7 +155,7 @@ sph_status sph_density_solve(sph_ctx *ctx, double *h_inout_dev, double *rho_out_
 sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_dev,
                             int32_t *count_out_dev, double *nw_out_dev, double *dnw_out_dev);
 
-/* k-nearest-neighbour smoothing lengths: the Subfind form of the density loop (Sec. IV-C and
+/* k-nearest-neighbour smoothing lengths: the Subfind form of the density loop (Sec. IV-D and
  * Listing 3), where each particle's neighbour list is put in order of distance and its K
  * nearest entries interact.  For every particle of the last sph_sort:
  *   h_i     = distance to the K-th nearest particle, the particle itself counted first;

@@ -14,7 +14,7 @@ evaluate(...)                one fixed-h density evaluation      (Eq. 1, Listing
 solve(...)                   the h iteration on one particle set (Sec. IV-A, Listing 3)
 batch_solve(...)             the same over independent non-periodic groups
 knn(...)                     h = distance to the K-th nearest particle, rho at that h
-                             (Sec. IV-C, the selection of the K nearest)
+                             (Sec. IV-D, the selection of the K nearest)
 """
 from __future__ import annotations
 

@@ -35,7 +35,7 @@
  *      pass limit     after max_iter evaluations -> status "not converged".
  *    An unconverged particle reports the last h it was evaluated at, with the density
  *    and counts of that evaluation.
- *  - The k-nearest-neighbour form of h (Sec. IV-C): h_i = distance to the K-th nearest
+ *  - The k-nearest-neighbour form of h (Sec. IV-D): h_i = distance to the K-th nearest
  *    particle, rho_i by Eq. (1) at that h (oracle_knn).
  *
  * Neighbour search: a stack of uniform FP64 bucket grids (cell size box / 2^k).  For a
@@ -581,7 +581,7 @@ int oracle_batch_solve(int64_t n_groups, const int64_t *offsets, const double *x
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* k-nearest-neighbour smoothing length (Sec. IV-C)                                       */
+/* k-nearest-neighbour smoothing length (Sec. IV-D)                                       */
 /* ------------------------------------------------------------------------------------ */
 
 static int cmp_double(const void *a, const void *b)
@@ -591,7 +591,7 @@ static int cmp_double(const void *a, const void *b)
 }
 
 /* The Subfind form of the density loop (Listing 1 inside the loop of Listing 3, with the
- * selection of Sec. IV-C): the neighbour list of a particle is put in order of distance
+ * selection of Sec. IV-D): the neighbour list of a particle is put in order of distance
  * and its first K entries are the ones that interact.  Read as a definition:
  *   h_i   = the K-th smallest of the distances r_ij over all j, the particle itself
  *           included (r_ii = 0 is the first), with r_ij the minimum-image distance when

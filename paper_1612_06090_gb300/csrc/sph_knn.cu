@@ -1,4 +1,4 @@
-// sph_knn.cu -- k-nearest-neighbour smoothing lengths (Sec. IV-C): one warp per target streams
+// sph_knn.cu -- k-nearest-neighbour smoothing lengths (Sec. IV-D): one warp per target streams
 // the candidates inside the target's search radius, keeps their squared distances in a buffer
 // cut back to its K nearest when full, and selects the K-th with a warp radix select.
 #include <climits>
@@ -12,7 +12,7 @@ namespace sph {
 
 namespace {
 
-// ---- k-nearest-neighbour smoothing length (Sec. IV-C) --------------------------------------
+// ---- k-nearest-neighbour smoothing length (Sec. IV-D) --------------------------------------
 //
 // The Subfind form of the density loop orders each particle's neighbour list by distance and
 // keeps the K nearest.  Here one warp owns one target: it streams the candidates inside the

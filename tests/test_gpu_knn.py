@@ -1,4 +1,4 @@
-"""GPU parity of the k-nearest-neighbour smoothing length (Sec. IV-C) through the C ABI.
+"""GPU parity of the k-nearest-neighbour smoothing length (Sec. IV-D) through the C ABI.
 
 h_i is the distance to the K-th nearest particle (the particle itself first) and rho_i the
 density at that h.  FP64 forms every squared distance exactly as the oracle does and the

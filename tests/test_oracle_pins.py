@@ -407,7 +407,7 @@ def test_wendland_c6_solve_converges_in_band():
     assert np.all(np.abs(r["nw"] - 295.0) <= 5.0)
 
 
-# ---- k-nearest-neighbour smoothing length (Sec. IV-C) --------------------------------------
+# ---- k-nearest-neighbour smoothing length (Sec. IV-D) --------------------------------------
 
 def _lattice(side):
     """Simple cubic lattice of side^3 particles with spacing a = 1/side in the unit periodic box
