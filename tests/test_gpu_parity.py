@@ -418,3 +418,44 @@ def test_wendland_c6_solve_clusters_sampled(precision):
     check_solve(wl.pos, wl.mass, wl.box, True, 295.0, 5.0, gs, o, tg, rtol=1e-12 if fp64 else 1e-5,
                 delta=(1e-9 if fp64 else 1e-5) * 295.0, max_mismatch_frac=0.03, count_exact=fp64,
                 kernel="wendland_c6")
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_mass_scaling_gpu(precision):
+    # rho is linear in the masses and h does not depend on them: scaling every mass by a power
+    # of two scales rho by exactly that power (every product and sum scales without rounding)
+    # and leaves h, N_w and the counts bit for bit unchanged -- for the band solve and for kNN
+    wl = inputs.make("c2", n=8192)
+    a = gpu_solve(wl.pos, wl.mass, wl.h0, precision)
+    b = gpu_solve(wl.pos, wl.mass * 8.0, wl.h0, precision)
+    np.testing.assert_array_equal(a["h"], b["h"])
+    np.testing.assert_array_equal(a["nw"], b["nw"])
+    np.testing.assert_array_equal(a["count"], b["count"])
+    np.testing.assert_array_equal(a["rho"] * 8.0, b["rho"])
+    for m in (wl.mass, wl.mass * 0.25):
+        s = B.Solver(wl.n, precision=precision)
+        s.sort(T(wl.pos), T(m))
+        r = s.knn(64, torch.zeros(wl.n, dtype=torch.float64, device=DEV))
+        torch.cuda.synchronize()
+        s.close()
+        if m is wl.mass:
+            ka = {k: np_(v) for k, v in r.items() if torch.is_tensor(v)}
+        else:
+            np.testing.assert_array_equal(np_(r["h"]), ka["h"])
+            np.testing.assert_array_equal(np_(r["count"]), ka["count"])
+            np.testing.assert_array_equal(np_(r["rho"]) * 4.0, ka["rho"])
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_periodic_translation_invariance_gpu(precision):
+    # shifting every particle by a quarter box (wrapped) changes the Morton order, the cells and
+    # the work items completely; the answer may only change by rounding
+    wl = inputs.make("c2", n=8192)
+    shifted = np.mod(wl.pos + np.array([[0.25], [0.5], [0.75]]), 1.0)
+    a = gpu_solve(wl.pos, wl.mass, wl.h0, precision)
+    b = gpu_solve(shifted, wl.mass, wl.h0, precision)
+    tol = 1e-12 if precision == FP64 else 1e-5
+    same = rel_err(b["h"], a["h"]) <= tol  # band-edge particles may take another valid branch
+    assert same.mean() > 0.999
+    assert np.max(rel_err(b["rho"][same], a["rho"][same])) <= tol
+    assert np.all(np.abs(b["nw"] - wl.nngb) <= wl.tol + 1e-5 * wl.nngb)
