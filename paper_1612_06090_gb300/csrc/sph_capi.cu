@@ -240,6 +240,7 @@ SolveArgs solve_args(sph_ctx *c)
     a.direct_pct = c->tuning.direct_pct;
     a.free_first = (c->kl.seg_bits == 0 && c->params.precision != SPH_PREC_FP64 &&
                     c->tuning.direct_pct == 0) ? 1 : 0;
+    a.cubic = (c->seg_host.q[0] == c->seg_host.q[1] && c->seg_host.q[1] == c->seg_host.q[2]) ? 1 : 0;
     a.launches = &c->launches;
     return a;
 }

@@ -75,6 +75,7 @@ struct SolveArgs {
     int kernel;                // sph_kernel: 0 M4 cubic spline, 1 Wendland C6
     int free_first;            // 1: the first pass of a solve from one common h runs the
                                // branch-free FP32 pair loop (periodic FP32 direct solves)
+    int cubic;                 // 1: equal fixed-point quanta in x, y, z (read by the kNN pass)
     int *launches;
     cudaEvent_t dens_ev[2];    // optional events recorded around the density launch
 };

@@ -87,11 +87,11 @@ __device__ __forceinline__ U radix_select(const U *__restrict__ keys, int c, int
 }
 
 // rho, N_w and the count at h over the buffered candidates (the target's own entry included),
-// in the precision of the pass.  FP64: the oracle's pair terms; FP32: single-precision terms and
+// in the precision of the pass (FP32 entries are squared distances in units of u2).  FP64: the oracle's pair terms; FP32: single-precision terms and
 // sums (at most K - 1 + ties terms per target).
 template <bool kF64, typename T>
 __device__ void knn_density(const SolveArgs &a, int p, double h, const T *__restrict__ buf,
-                            const int *__restrict__ bidx, int c)
+                            const int *__restrict__ bidx, int c, float u2)
 {
     const int lane = lane_id();
     const bool c6 = a.kernel != 0;
@@ -138,7 +138,7 @@ __device__ void knn_density(const SolveArgs &a, int p, double h, const T *__rest
         float smw = 0.f, sw = 0.f;
         int cnt = 0;
         for (int i = lane; i < c; i += 32) {
-            const float r2 = (float)buf[i];
+            const float r2 = (float)buf[i] * u2;  // FP32 entries are in units of u2
             if (r2 < h2) {
                 const float q = sqrtf(r2) * hinv;
                 float w;
@@ -171,7 +171,9 @@ __device__ void knn_density(const SolveArgs &a, int p, double h, const T *__rest
     }
 }
 
-template <bool kF64>
+// kCubic: the three fixed-point quanta are equal (a cubic box), so squared distances are formed
+// in units of q^2 from the integer offsets directly and converted once per target.
+template <bool kF64, bool kCubic>
 __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
     k_knn(SolveArgs a, const int32_t *__restrict__ todo, int K)
 {
@@ -220,7 +222,12 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
             const float cc[3] = {0.f, 0.f, 0.f};
             item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, cc, ball2, qf, rr);
         }
-        const float H2f = Hf * Hf;
+        // FP32 distances are in units of u2 = q^2 when the box is cubic, else in box units
+        const float uq = kCubic ? qf[0] : 1.0f;
+        const float u2 = uq * uq;
+        const float Hu = Hf / uq;
+        const float H2f = Hu * Hu;
+        const float ball2u = kCubic ? ball2 / u2 : ball2;
         const double H2 = __dmul_rn(H, H);
         double4_32a ti = make_double4_32a(0, 0, 0, 0);
         if (kF64) ti = a.pdbl[p];
@@ -243,8 +250,8 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
         // The buffer holds candidates inside H.  When it would overflow it is cut to the
         // entries at or below its K-th smallest value tau; from then on only candidates at or
         // below tau enter (tau only falls, so every value below the final tau stays, and the
-        // K-th smallest of the buffer at the end is the K-th smallest inside H).
-        int seen = 0;  // candidates strictly inside H
+        // K-th smallest of the buffer at the end is the K-th smallest inside H).  Until the
+        // first cut the buffer holds every candidate inside H, so c is their count.
         int c = 0;     // entries in the buffer
         bool cut = false, stuck = false;
         T tau = 0;
@@ -279,11 +286,12 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
                 const int rj[3] = {(int32_t)(Pj.x - G3.X0[0]), (int32_t)(Pj.y - G3.X0[1]),
                                    (int32_t)(Pj.z - G3.X0[2])};
                 {
-                    const float fx = (float)rj[0] * qf[0], fy = (float)rj[1] * qf[1],
-                                fz = (float)rj[2] * qf[2];
+                    const float fx = kCubic ? (float)rj[0] : (float)rj[0] * qf[0];
+                    const float fy = kCubic ? (float)rj[1] : (float)rj[1] * qf[1];
+                    const float fz = kCubic ? (float)rj[2] : (float)rj[2] * qf[2];
                     const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                     if (kF64) {
-                        if (r2f <= ball2) {
+                        if (r2f <= ball2u) {
                             const double4_32a cj = a.pdbl[j];
                             double dx = __dsub_rn(cj.x, ti.x);
                             double dy = __dsub_rn(cj.y, ti.y);
@@ -304,7 +312,6 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
                     }
                 }
             }
-            seen += __popc(__ballot_sync(kFull, in));
             bool keep = in && (!cut || r2 <= tau);
             unsigned m = __ballot_sync(kFull, keep);
             if (c + __popc(m) > cap && !stuck) {
@@ -348,22 +355,22 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
           }
         }
         tests += (unsigned long long)total;
-        listed += (unsigned long long)seen;
+        listed += (unsigned long long)c;
         __syncwarp();
 
         int alive = 0;
-        if (seen >= K && !stuck) {
+        if ((cut || c >= K) && !stuck) {
             const U key = radix_select<U>((const U *)buf, c, K, hist);
             T r2k;
             memcpy(&r2k, &key, sizeof(T));
-            const double h = kF64 ? __dsqrt_rn((double)r2k) : sqrt((double)r2k);
+            const double h = kF64 ? __dsqrt_rn((double)r2k) : sqrt((double)r2k) * (double)uq;
             if (S.periodic && h >= S.half_box) {
                 exceeded++;
                 if (lane == 0) a.e_h[p] = H;
             } else {
                 // Eq. 1 at h from the buffer: every particle with r < h is in it (all entries
                 // at or below tau >= r_K^2 were kept)
-                knn_density<kF64>(a, p, h, buf, bidx, c);
+                knn_density<kF64>(a, p, h, buf, bidx, c, u2);
             }
         } else {
             // bracket: lo holds fewer than K candidates, hi a radius where the buffer could not
@@ -371,13 +378,13 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
             // with both sides known the bracket is halved geometrically (the count is monotone
             // in H, so this ends even where density changes steeply)
             double lo = a.hlo[p], hi = a.hhi[p];
-            if (seen < K) lo = H;
+            if (!cut) lo = H;  // fewer than K inside H
             else hi = H;  // stuck: thousands of equal distances inside H
             double hn;
             if (lo > 0.0 && hi < HUGE_VAL) {
                 hn = sqrt(lo * hi);
-            } else if (seen < K) {
-                hn = H * fmin(fmax(cbrt(2.0 * K / (double)(seen > 0 ? seen : 1)), 1.05), 4.0);
+            } else if (!cut) {
+                hn = H * fmin(fmax(cbrt(2.0 * K / (double)(c > 0 ? c : 1)), 1.05), 4.0);
             } else {
                 hn = H * 0.5;
             }
@@ -416,14 +423,21 @@ __global__ void __launch_bounds__(kKnnThreads, kF64 ? 2 : 3)
 
 }  // namespace
 
-template <bool kF64>
+template <bool kF64, bool kCubic>
 int knn_blocks_per_sm()
 {
     const int bytes = kKnnWarps * knn_warp_bytes<kF64>();
-    cudaFuncSetAttribute(k_knn<kF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_knn<kF64, kCubic>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_knn<kF64>, kKnnThreads, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_knn<kF64, kCubic>, kKnnThreads, bytes);
     return b > 0 ? b : 1;
+}
+
+template <bool kF64, bool kCubic>
+void knn_launch(const SolveArgs &a, const int32_t *todo, int k, int sms, cudaStream_t st)
+{
+    k_knn<kF64, kCubic><<<sms * knn_blocks_per_sm<kF64, kCubic>(), kKnnThreads,
+                          kKnnWarps * knn_warp_bytes<kF64>(), st>>>(a, todo, k);
 }
 
 int knn_capacity(int precision) { return precision == 0 ? knn_cap<true>() : knn_cap<false>(); }
@@ -433,12 +447,13 @@ cudaError_t launch_knn(const SolveArgs &a, const int32_t *todo, int k, cudaStrea
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (a.precision == 0)
-        k_knn<true><<<sms * knn_blocks_per_sm<true>(), kKnnThreads, kKnnWarps * knn_warp_bytes<true>(), st>>>(
-            a, todo, k);
-    else
-        k_knn<false><<<sms * knn_blocks_per_sm<false>(), kKnnThreads, kKnnWarps * knn_warp_bytes<false>(),
-                       st>>>(a, todo, k);
+    if (a.precision == 0) {
+        if (a.cubic) knn_launch<true, true>(a, todo, k, sms, st);
+        else knn_launch<true, false>(a, todo, k, sms, st);
+    } else {
+        if (a.cubic) knn_launch<false, true>(a, todo, k, sms, st);
+        else knn_launch<false, false>(a, todo, k, sms, st);
+    }
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }
