@@ -27,9 +27,30 @@ __device__ __forceinline__ int seg_of(uint64_t k, const KeyLayout &kl)
 // `big` marks targets whose cell plus h reaches half the periodic range; those form
 // single-target work items so every staged offset is a minimum-image offset.
 // (FP32 with margins that make `big` conservative; the level itself only steers efficiency)
+// Expected neighbours within h from the local density of the dense cell table: the target's
+// table cell, widened to coarser levels until it holds 8 particles.
+__device__ __forceinline__ float expected_neighbours(uint64_t k, float h, const SegInfo &S,
+                                                     const KeyLayout &kl, const int32_t *__restrict__ ctab)
+{
+    const int32_t *t = ctab + S.tab_off;
+    const int lc = S.level_c;
+    uint64_t m = (k & ((1ull << (3 * kl.lmax)) - 1ull)) >> (3 * (kl.lmax - lc));
+    int l = lc;
+    int cnt = t[m + 1] - t[m];
+    while (cnt < 8 && l > 0) {
+        l--;
+        m >>= 3;
+        const int sh = 3 * (lc - l);
+        cnt = t[(m + 1) << sh] - t[m << sh];
+    }
+    float vol = 1.f;
+    for (int d = 0; d < 3; d++) vol *= ldexpf((float)S.q[d], kl.coord_bits - l);
+    return (float)cnt / vol * (4.18879020f * h * h * h);
+}
+
 __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
                                           const KeyLayout &kl, int shift, int &lvl,
-                                          uint64_t &prefix, bool &big)
+                                          uint64_t &prefix, bool &big, const int32_t *ctab)
 {
     const int cb = kl.coord_bits;
     const float maxinv = (float)fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
@@ -37,6 +58,10 @@ __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
     const float edge = ldexpf(hu, -shift);
     int l = kl.lmax;
     while (l > 0 && (float)(1ll << (cb - l)) < edge) l--;
+    // first pass only (ctab given): a target whose starting h holds few neighbours groups two
+    // levels coarser, so neighbouring isolated targets share items instead of paying an item
+    // each (the todo list is still complete there, so consecutive targets are neighbours)
+    if (ctab && l >= 2 && expected_neighbours(k, h, S, kl, ctab) < 16.f) l -= 2;
     lvl = l;
     prefix = k >> (3 * (kl.lmax - l));
     big = S.periodic && ((float)(1ll << (cb - l)) + hu >= (float)(1ll << (cb - 1)));
@@ -173,13 +198,14 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
 {
     const int T = a.ds->pass_count;
     const bool dense = 8 * (int64_t)T >= a.n;
+    const int32_t *ctab0 = a.ds->pass == 0 ? a.ctab : nullptr;  // sparse-target rule in pass 0
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int p = todo[t];
         const uint64_t k = a.key[p];
         int l;
         uint64_t pre;
         bool big;
-        bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big);
+        bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big, ctab0);
         int head = (t % a.gmax == 0) || big;
         if (!head) {
             const int pp = todo[t - 1];
@@ -187,7 +213,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
             int lp;
             uint64_t prep;
             bool bigp;
-            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp);
+            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp, ctab0);
             if (dense) {
                 const int m = lp < l ? lp : l;
                 head = bigp || (l - lp > 1) || (lp - l > 1) ||
