@@ -339,7 +339,7 @@ def run_native(args):
     achieved = pairs * FLOP_PER_PAIR / (dens_ms / 1e3) / 1e12 if dens_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_density<2> (FP32 pair loop)", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": profiled_traffic() if args.config == "c2" and not args.n else None,
+            "traffic": profiled_traffic() if args.config == "c2" and not args.n and args.kernel == "m4" else None,
             "traffic_note": "mean DRAM bytes per density pass (ncu, profiles/density_fp32_c2_1M.md)",
             "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
             "flop_per_pair": FLOP_PER_PAIR, "pairs_per_step": pairs // max(1, len(st32)),

@@ -58,9 +58,9 @@ __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
     const float edge = ldexpf(hu, -shift);
     int l = kl.lmax;
     while (l > 0 && (float)(1ll << (cb - l)) < edge) l--;
-    // first pass only (ctab given): a target whose starting h holds few neighbours groups two
-    // levels coarser, so neighbouring isolated targets share items instead of paying an item
-    // each (the todo list is still complete there, so consecutive targets are neighbours)
+    // ctab given (first pass of batched groups): a target whose starting h holds few neighbours
+    // groups two levels coarser, so neighbouring isolated targets share items instead of paying
+    // an item each (the todo list is still complete there, so consecutive targets are neighbours)
     if (ctab && l >= 2 && expected_neighbours(k, h, S, kl, ctab) < 16.f) l -= 2;
     lvl = l;
     prefix = k >> (3 * (kl.lmax - l));
@@ -198,7 +198,8 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
 {
     const int T = a.ds->pass_count;
     const bool dense = 8 * (int64_t)T >= a.n;
-    const int32_t *ctab0 = a.ds->pass == 0 ? a.ctab : nullptr;  // sparse-target rule in pass 0
+    // the sparse-target rule: first pass of batched open groups (isolated halo particles)
+    const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
         const int p = todo[t];
         const uint64_t k = a.key[p];
