@@ -12,6 +12,7 @@ w(q), mqdw(q)                M4 shape w(q) and -q w'(q)          (Eq. 1 kernel)
 w_c6(q), mqdw_c6(q)          Wendland C6 shape (Sec. II-B kernel) and -q w'(q)
 evaluate(...)                one fixed-h density evaluation      (Eq. 1, Listing 1)
 solve(...)                   the h iteration on one particle set (Sec. IV-A, Listing 3)
+h_update(...)                one step of that iteration's h update
 batch_solve(...)             the same over independent non-periodic groups
 knn(...)                     h = distance to the K-th nearest particle, rho at that h
                              (Sec. IV-D, the selection of the K nearest)
@@ -99,6 +100,9 @@ def _load():
     lib.oracle_knn.restype = ctypes.c_int
     lib.oracle_knn.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int64, ip, ctypes.c_int, dp, dp, dp, ip, i32p, ctypes.c_int]
+    lib.oracle_h_update.restype = ctypes.c_double
+    lib.oracle_h_update.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    dp, dp]
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
     _lib = lib
@@ -144,6 +148,18 @@ def w_c6(q: float) -> float:
 def mqdw_c6(q: float) -> float:
     """-q w'(q) of the Wendland C6 shape; dN_w/dh = (1365/48)(1/h) sum_j mqdw_c6(q_j)."""
     return float(_load().oracle_mqdw_c6(float(q)))
+
+
+def h_update(h, nw, dnw, nngb, h_lo=0.0, h_hi=float("inf")):
+    """One step of the h iteration from an evaluation (N_w, N_w') at h outside the band.
+
+    h_lo / h_hi: the bracket before this evaluation (0 and +inf when unset).  Returns
+    (next h, h_lo, h_hi) with the bracket updated by this evaluation.
+    """
+    lo = ctypes.c_double(h_lo)
+    hi = ctypes.c_double(h_hi)
+    hn = _load().oracle_h_update(float(h), float(nw), float(dnw), float(nngb), ctypes.byref(lo), ctypes.byref(hi))
+    return float(hn), lo.value, hi.value
 
 
 KERNELS = {"m4": 0, "wendland_c6": 1}

@@ -419,6 +419,26 @@ int oracle_eval(int64_t n, const double *x, const double *y, const double *z, co
     return 0;
 }
 
+/* One step of the h iteration for a particle evaluated at h = hc that is not yet in the
+ * band: the bracket takes hc (below the target -> lower bound, else upper bound; an unset
+ * lower bound is 0, an unset upper bound +inf), then the Newton point
+ * hc - (N_w - Nngb) / N_w' is returned when N_w' > 0 and it lies strictly inside the
+ * bracket and within [hc/2, 2 hc]; otherwise the bracket midpoint when both bounds are
+ * set, hc * 2^(1/3) with only a lower bound, hc / 2^(1/3) with only an upper bound. */
+double oracle_h_update(double hc, double nw, double dnw, double nngb, double *hlo, double *hhi)
+{
+    if (nw < nngb) *hlo = hc;
+    else *hhi = hc;
+    if (dnw > 0.0) {
+        double hn = hc - (nw - nngb) / dnw;
+        if (hn > *hlo && hn < *hhi && hn >= 0.5 * hc && hn <= 2.0 * hc) return hn;
+    }
+    int has_lo = *hlo > 0.0, has_hi = *hhi < HUGE_VAL;
+    if (has_lo && has_hi) return 0.5 * (*hlo + *hhi);
+    if (has_lo) return hc * ORACLE_GROWTH;
+    return hc / ORACLE_GROWTH;
+}
+
 /* Solve statistics, mirrored by a ctypes structure in oracle/__init__.py. */
 typedef struct {
     int32_t passes;
@@ -493,20 +513,7 @@ static int solve_set(const pset *ps, int64_t n_targets, const int64_t *targets, 
                 status_out[t] = ORC_OK;
                 continue;
             }
-            if (nw < nngb) hlo[t] = hc;
-            else hhi[t] = hc;
-            double hn = hc;
-            int take = 0;
-            if (dnw > 0.0) {
-                hn = hc - (nw - nngb) / dnw;
-                take = hn > hlo[t] && hn < hhi[t] && hn >= 0.5 * hc && hn <= 2.0 * hc;
-            }
-            if (!take) {
-                int has_lo = hlo[t] > 0.0, has_hi = hhi[t] < HUGE_VAL;
-                if (has_lo && has_hi) hn = 0.5 * (hlo[t] + hhi[t]);
-                else if (has_lo) hn = hc * ORACLE_GROWTH;
-                else hn = hc / ORACLE_GROWTH;
-            }
+            double hn = oracle_h_update(hc, nw, dnw, nngb, &hlo[t], &hhi[t]);
             if (ps->periodic && hn >= half_box) {
                 status_out[t] = ORC_EXCEEDS_BOX;
                 continue;

@@ -120,6 +120,25 @@ def test_adversarial_positions_on_cell_faces_and_box_edges():
     np.testing.assert_allclose(o["rho"], b["rho"], rtol=1e-13)
 
 
+def test_non_cubic_periodic_box_matches_brute_force():
+    # box lengths differ per axis: each axis wraps with its own length
+    box = (1.0, 0.5, 2.0)
+    rng = np.random.default_rng(12)
+    pos = rng.uniform(0.0, 1.0, size=(3, 1500)) * np.array(box)[:, None]
+    mass = rng.uniform(0.5, 1.5, size=1500)
+    h = rng.uniform(0.05, 0.24, size=1500)
+    o = oracle.evaluate(pos, mass, h, box=box)
+    b = brute.evaluate(pos, mass, h, box=box)
+    np.testing.assert_array_equal(o["count"], b["count"])
+    np.testing.assert_allclose(o["rho"], b["rho"], rtol=1e-13)
+    np.testing.assert_allclose(o["dnw"], b["dnw"], rtol=1e-12)
+    spatial = pytest.importorskip("scipy.spatial")
+    tg = np.arange(0, 1500, 11)
+    r = oracle.knn(pos, mass, 40, box=box, targets=tg)
+    d, _ = spatial.cKDTree(pos.T, boxsize=np.array(box)).query(pos.T[tg], k=40)
+    np.testing.assert_allclose(r["h"], d[:, -1], rtol=1e-14)
+
+
 def test_non_periodic_matches_brute_force():
     rng = np.random.default_rng(8)
     pos = rng.normal(0.0, 3.0, size=(3, 700))
@@ -330,17 +349,206 @@ def test_two_particle_root_closed_form():
     np.testing.assert_allclose(res["h"], h_star, rtol=1e-9)
 
 
+GROWTH = 1.2599210498948732  # 2^(1/3) as the double literal of the update rule
+
+
+def _trajectory(pos, mass, h0, targets, passes, **kw):
+    """h_k, status and outputs after k + 1 passes, for k < passes.
+
+    A particle still unconverged after k + 1 passes reports the h of its last evaluation,
+    so solves stopped after 1, 2, ... passes expose the whole sequence of evaluated h.
+    """
+    runs = [oracle.solve(pos, mass, h0, targets=targets, max_iter=k + 1, **kw) for k in range(passes)]
+    return runs, np.array([r["h"] for r in runs]), np.array([r["status"] for r in runs])
+
+
+@pytest.mark.parametrize("case", ["uniform_scattered_starts", "clustered_common_start", "tight_clumps"])
+def test_update_rule_along_trajectories(case):
+    # Every step of the h iteration, checked against what the update rule fixes:
+    #  - h moves towards the band (up when N_w < Nngb, down when N_w > Nngb);
+    #  - it stays strictly inside the bracket of all earlier evaluations;
+    #  - it is the Newton point h - (N_w - Nngb)/N_w' when that lies inside the bracket and
+    #    within [h/2, 2h], otherwise the bracket midpoint, or h * 2^(1/3) (only a lower
+    #    bound) or h / 2^(1/3) (only an upper bound).
+    # N_w and N_w' at each evaluated h come from the fixed-h evaluation, which is pinned by
+    # brute force and by finite differences above.  Each kind of step must occur.
+    nngb, tol = 64.0, 0.5
+    if case == "uniform_scattered_starts":
+        wl = inputs.make("c1")
+        tg = np.arange(0, wl.n, 17)
+        h0 = wl.h0[tg] * np.random.default_rng(5).choice([0.2, 0.45, 1.0, 2.2, 4.0], size=tg.size)
+        pos, mass = wl.pos, wl.mass
+    elif case == "clustered_common_start":
+        wl = inputs.make("c2", n=16384)
+        tg = np.random.default_rng(6).choice(wl.n, size=240, replace=False)
+        h0 = wl.h0[tg]
+        pos, mass = wl.pos, wl.mass
+    else:
+        # 64 clumps of 8 (spread 2e-3) on a lattice of spacing 1/4: from h0 = 0.1 every
+        # target sees N_w ~ 85 > Nngb with N_w' nearly zero, so Newton is refused and h
+        # shrinks until the clump's own profile brackets the root
+        g = np.arange(4) * 0.25 + 0.125
+        c = np.stack([a.ravel() for a in np.meshgrid(g, g, g, indexing="ij")])
+        pos = np.mod(np.repeat(c, 8, axis=1) + np.random.default_rng(7).normal(0, 2e-3, (3, 512)), 1.0)
+        mass = np.full(512, 1.0 / 512)
+        tg = np.arange(0, 512, 3)
+        h0 = np.full(tg.size, 0.1)
+    P = 14
+    runs, hs, st = _trajectory(pos, mass, h0, tg, P, nngb=nngb, tol=tol)
+    ev = [oracle.evaluate(pos, mass, hs[k], targets=tg) for k in range(P)]
+    kinds = {"newton": 0, "midpoint": 0, "grow": 0, "shrink": 0}
+    pairs = 0
+    for k in range(P):
+        # the outputs of an unconverged particle describe its last evaluation
+        live = st[k] == oracle.STATUS_NOT_CONVERGED
+        np.testing.assert_array_equal(runs[k]["rho"][live], ev[k]["rho"][live])
+        np.testing.assert_array_equal(runs[k]["nw"][live], ev[k]["nw"][live])
+        np.testing.assert_array_equal(runs[k]["count"][live], ev[k]["count"][live])
+        # pair_evals sums the neighbour counts of every evaluation made
+        evaluated = np.ones(tg.size, bool) if k == 0 else st[k - 1] == oracle.STATUS_NOT_CONVERGED
+        pairs += int(ev[k]["count"][evaluated].sum())
+        assert runs[k]["stats"]["pair_evals"] == pairs
+        n_eval = int(evaluated.sum())
+        if n_eval:
+            assert runs[k]["stats"]["passes"] == k + 1
+            assert runs[k]["stats"]["todo_per_pass"][k] == n_eval
+        else:
+            assert runs[k]["stats"]["passes"] <= k
+        if k == P - 1:
+            break
+        for p in np.nonzero(live)[0]:
+            h, nw, dnw = hs[k][p], ev[k]["nw"][p], ev[k]["dnw"][p]
+            assert abs(nw - nngb) > tol
+            below = [hs[j][p] for j in range(k + 1) if ev[j]["nw"][p] < nngb]
+            above = [hs[j][p] for j in range(k + 1) if ev[j]["nw"][p] >= nngb]
+            lo = max(below) if below else 0.0
+            hi = min(above) if above else math.inf
+            hn = hs[k + 1][p]
+            assert (hn > h) == (nw < nngb)
+            assert lo < hn < hi
+            newton = h - (nw - nngb) / dnw if dnw > 0 else None
+            if newton is not None and lo < newton < hi and 0.5 * h <= newton <= 2.0 * h:
+                assert hn == newton
+                kinds["newton"] += 1
+            elif below and above:
+                assert hn == 0.5 * (lo + hi)
+                kinds["midpoint"] += 1
+            elif below:
+                assert hn == h * GROWTH
+                kinds["grow"] += 1
+            else:
+                assert hn == h / GROWTH
+                kinds["shrink"] += 1
+    want = {"uniform_scattered_starts": ("newton", "grow"), "clustered_common_start": ("newton",),
+            "tight_clumps": ("newton", "shrink")}[case]
+    for kind in want:
+        assert kinds[kind] > 0, kinds
+
+
+@pytest.mark.parametrize("h,nw,dnw,lo,hi,expect,bracket", [
+    # Newton accepted: 1 + (64 - 60)/40
+    (1.0, 60.0, 40.0, 0.0, math.inf, 1.1, (1.0, math.inf)),
+    # the Newton point 2.0 lies beyond the upper bound 1.5: midpoint of [1, 1.5]
+    (1.0, 60.0, 4.0, 0.0, 1.5, 1.25, (1.0, 1.5)),
+    # Newton point equal to the upper bound: the bracket is open, so the midpoint
+    (1.0, 62.0, 4.0, 0.0, 1.5, 1.25, (1.0, 1.5)),
+    # Newton point exactly 2h or exactly h/2: accepted (closed step limits)
+    (1.0, 62.0, 2.0, 0.0, math.inf, 2.0, (1.0, math.inf)),
+    (1.0, 66.0, 4.0, 0.0, math.inf, 0.5, (0.0, 1.0)),
+    # beyond 2h with only a lower bound: grow by 2^(1/3)
+    (1.0, 10.0, 1.0, 0.0, math.inf, GROWTH, (1.0, math.inf)),
+    # below h/2 with only an upper bound: shrink by 2^(1/3)
+    (1.0, 100.0, 10.0, 0.0, math.inf, 1.0 / GROWTH, (0.0, 1.0)),
+    # no slope (no neighbour but the particle itself): midpoint when both bounds are set
+    (0.8, 32.0 / 3.0, 0.0, 0.0, 1.0, 0.9, (0.8, 1.0)),
+    (0.8, 32.0 / 3.0, 0.0, 0.0, math.inf, 0.8 * GROWTH, (0.8, math.inf)),
+    # the Newton point falls below the lower bound: midpoint
+    (1.2, 70.0, 20.0, 1.0, math.inf, 1.1, (1.0, 1.2)),
+])
+def test_h_update_branches(h, nw, dnw, lo, hi, expect, bracket):
+    # Each branch of the update rule on inputs whose next h follows from the rule's
+    # statement by hand; the solve applies this same step to every unconverged particle.
+    hn, lo2, hi2 = oracle.h_update(h, nw, dnw, 64.0, lo, hi)
+    assert hn == pytest.approx(expect, rel=1e-15)
+    assert (lo2, hi2) == bracket
+
+
+def test_newton_steps_converge_quadratically_at_the_closed_form_rate():
+    # Two particles a distance r apart and Nngb = 16: N_w(h) = (32/3)(1 + w(r/h)) on the inner
+    # piece of w, so F(h) = N_w(h) - 16 is a cubic in r/h with a simple root h*.  Newton's
+    # method gives e_{k+1} = F''(h*) / (2 F'(h*)) e_k^2 + O(e_k^3); the ratio is computed here
+    # symbolically from the kernel polynomial, not from the oracle.
+    sympy = pytest.importorskip("sympy")
+    r_sep = 0.05
+    hh, q = sympy.symbols("h q", positive=True)
+    w_inner = 1 - 6 * q**2 + 6 * q**3
+    F = sympy.Rational(32, 3) * (1 + w_inner.subs(q, r_sep / hh)) - 16
+    q_star = [x for x in sympy.Poly(6 * q**3 - 6 * q**2 + sympy.Rational(1, 2), q).nroots(n=30)
+              if x.is_real and 0 < x <= sympy.Rational(1, 2)]
+    assert len(q_star) == 1
+    h_star = float(r_sep / q_star[0])
+    c = float((sympy.diff(F, hh, 2) / (2 * sympy.diff(F, hh))).subs(hh, r_sep / q_star[0])) * h_star
+    pos = np.array([[0.4, 0.4 + r_sep], [0.5, 0.5], [0.5, 0.5]])
+    for f in (1.05, 0.97, 1.02):
+        _, hs, st = _trajectory(pos, np.array([1.0, 1.0]), np.array([f * h_star]), np.array([0]), 7,
+                                box=(0, 0, 0), periodic=False, nngb=16.0, tol=1e-13)
+        assert st[5][0] == oracle.STATUS_CONVERGED  # converged within six evaluations
+        e = (hs[:, 0] - h_star) / h_star
+        ratios = [e[k + 1] / e[k] ** 2 for k in range(4) if 1e-7 < abs(e[k]) < 0.06]
+        assert len(ratios) >= 2
+        for rt in ratios:
+            assert rt == pytest.approx(c, rel=0.12)
+
+
+def test_band_edges_are_inclusive():
+    # One isolated particle (open boundaries): N_w = 32/3 exactly at every h.  With the band
+    # edge exactly on it the particle converges at once; a hair inside, it never does.
+    pos = np.array([[0.5], [0.5], [0.5]])
+    nw = 32.0 / 3.0
+    for nngb in (10.0, 11.0):
+        tol = abs(nw - nngb)  # exact (Sterbenz)
+        kw = dict(box=(0, 0, 0), periodic=False, nngb=nngb, max_iter=5)
+        r = oracle.solve(pos, np.array([1.0]), np.array([0.1]), tol=tol, **kw)
+        assert r["status"][0] == oracle.STATUS_CONVERGED and r["stats"]["passes"] == 1
+        assert r["h"][0] == 0.1
+        r = oracle.solve(pos, np.array([1.0]), np.array([0.1]), tol=np.nextafter(tol, 0.0), **kw)
+        assert r["status"][0] == oracle.STATUS_NOT_CONVERGED and r["stats"]["passes"] == 5
+
+
+def test_a_proposal_of_half_the_box_stops_the_particle():
+    # h must stay below half the periodic box: a proposed h equal to L/2 is refused before it
+    # is evaluated.  h0 is the double whose 2^(1/3) growth step lands exactly on 0.5.
+    h0 = 0.39685026299204984
+    assert h0 * GROWTH == 0.5
+    r = oracle.solve(np.array([[0.2], [0.2], [0.2]]), np.array([1.0]), np.array([h0]))
+    assert r["status"][0] == oracle.STATUS_EXCEEDS_BOX
+    assert r["stats"]["passes"] == 1
+    assert r["h"][0] == h0
+    just_below = np.nextafter(h0, 0.0)
+    assert just_below * GROWTH < 0.5
+    r = oracle.solve(np.array([[0.2], [0.2], [0.2]]), np.array([1.0]), np.array([just_below]))
+    assert r["stats"]["passes"] == 2 and r["h"][0] == just_below * GROWTH
+
+
 def test_batch_equals_groups_solved_alone():
     wl = inputs.plummer_groups(n_groups=12, nmin=32, nmax=600, seed=21)
     r = oracle.batch_solve(wl.offsets, wl.pos, wl.mass, wl.h0, wl.nngb, wl.tol)
+    passes, pairs, todo = 0, 0, np.zeros(64, dtype=np.int64)
     for g in range(wl.n_groups):
         s, e = wl.offsets[g], wl.offsets[g + 1]
         a = oracle.solve(wl.pos[:, s:e], wl.mass[s:e], wl.h0[s:e], box=(0, 0, 0), periodic=False,
                          nngb=wl.nngb[g], tol=wl.tol[g])
         np.testing.assert_array_equal(a["h"], r["h"][s:e])
         np.testing.assert_array_equal(a["rho"], r["rho"][s:e])
+        passes = max(passes, a["stats"]["passes"])
+        pairs += a["stats"]["pair_evals"]
+        todo[: a["stats"]["passes"]] += a["stats"]["todo_per_pass"]
     assert np.all(r["status"] == 0)
     assert np.all(np.abs(r["nw"] - 32.0) <= 1.0)
+    # the batch runs as long as its slowest group; the work adds up over the groups
+    assert r["stats"]["passes"] == passes
+    assert r["stats"]["pair_evals"] == pairs
+    assert r["stats"]["todo_per_pass"] == todo[:passes].tolist()
 
 
 def test_batch_group_brute_force_at_solution():
@@ -482,3 +690,10 @@ def test_knn_exceeds_box_and_argument_range():
     for k in (1, 28):
         with pytest.raises(ValueError):
             oracle.knn(pos, m, k)
+    # a K-th distance of exactly half the box is already beyond the periodic limit
+    two = np.array([[0.0, 0.5], [0.0, 0.0], [0.0, 0.0]])
+    r = oracle.knn(two, np.ones(2), 2)
+    assert np.all(r["h"] == 0.5) and np.all(r["status"] == 2)
+    two[0, 1] = 0.375
+    r = oracle.knn(two, np.ones(2), 2)
+    assert np.all(r["h"] == 0.375) and np.all(r["status"] == 0)
