@@ -7,6 +7,7 @@
 // binary search on the keys below it.  The gather into a compact sorted SoA plays the role
 // of the paper's AoS->SoA gather (Sec. IV-B).
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 #include "sph_common.cuh"
@@ -24,23 +25,43 @@ constexpr int kKeysPerThread = kTileKeys / kSortThreads;
 constexpr int kWarpKeys = kTileKeys / (kSortThreads / 32);  // contiguous keys ranked by one warp
 static_assert(kSortThreads == kRadixBins, "one thread per digit in the tile offsets");
 
-// Periodic fixed point: nearest multiple of q = L / 2^32, wrapped (L itself maps to 0).
+// FP64 instructions issue at a small fraction of the FP32 rate on this GPU, so the key and
+// gather kernels spend them only on the one multiply per coordinate that exact fixed point
+// needs; rounding, wrapping and the input checks use a conversion and integer operations.
+
+// Periodic fixed point: nearest multiple of q = L / 2^32 (ties to even), wrapped (L itself
+// maps to 0).  The conversion saturates (negatives give 0), the wrap of 2^32 to 0 is the
+// truncation to 32 bits, and a position outside [0, L) is flagged by the caller.
 __device__ __forceinline__ uint32_t fix_periodic(double x, double inv_q)
 {
-    double t = rint(x * inv_q);
-    if (!(t >= 0.0)) t = 0.0;  // also catches NaN (flagged separately)
-    if (t >= 4294967296.0) t -= 4294967296.0;
-    if (t >= 4294967296.0) t = 0.0;
-    return (uint32_t)(unsigned long long)t;
+    return (uint32_t)__double2ull_rn(x * inv_q);
 }
 
 // Open boundaries: nearest multiple of q above the origin, clamped to [0, 2^31).
 __device__ __forceinline__ uint32_t fix_open(double x, double origin, double inv_q)
 {
-    double t = rint((x - origin) * inv_q);
-    if (!(t >= 0.0)) t = 0.0;
-    if (t > 2147483647.0) t = 2147483647.0;
-    return (uint32_t)t;
+    const long long t = __double2ll_rn((x - origin) * inv_q);  // saturating conversion
+    return (uint32_t)(t < 0 ? 0ll : t > 2147483647ll ? 2147483647ll : t);
+}
+
+// 0 <= x < L on the IEEE-754 bit patterns (L positive and finite; -0.0 counts as 0): a
+// non-negative double orders like its bits, and NaN, infinities and negatives fail.
+__device__ __forceinline__ bool in_range_bits(double x, long long l_bits)
+{
+    const long long b = __double_as_longlong(x);
+    return (unsigned long long)b < (unsigned long long)l_bits || b == LLONG_MIN;
+}
+
+// 0 < m <= DBL_MAX on the bit pattern.
+__device__ __forceinline__ bool positive_finite_bits(double m)
+{
+    return (unsigned long long)__double_as_longlong(m) - 1ull < 0x7fefffffffffffffull;
+}
+
+// |x| <= DBL_MAX on the bit pattern (not NaN, not infinite).
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) <= 0x7fefffffffffffffull;
 }
 
 __global__ void k_keys_periodic(int64_t n, const double *__restrict__ pos,
@@ -50,13 +71,15 @@ __global__ void k_keys_periodic(int64_t n, const double *__restrict__ pos,
                                 DevState *ds)
 {
     const int shift = kl.coord_bits - kl.lmax;
+    const long long bx = __double_as_longlong(box_x), by = __double_as_longlong(box_y),
+                    bz = __double_as_longlong(box_z);
     int bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double x = pos[i], y = pos[n + i], z = pos[2 * n + i], m = mass[i];
-        if (!(x >= 0.0 && x < box_x && y >= 0.0 && y < box_y && z >= 0.0 && z < box_z))
+        if (!(in_range_bits(x, bx) && in_range_bits(y, by) && in_range_bits(z, bz)))
             bad |= kBadPosition;
-        if (!(m > 0.0 && m <= DBL_MAX)) bad |= kBadMass;
+        if (!positive_finite_bits(m)) bad |= kBadMass;
         uint32_t X = fix_periodic(x, seg.inv_q[0]);
         uint32_t Y = fix_periodic(y, seg.inv_q[1]);
         uint32_t Z = fix_periodic(z, seg.inv_q[2]);
@@ -91,8 +114,8 @@ __global__ void k_keys_open(int64_t n, const double *__restrict__ pos,
         const int g = group_of(offsets, n_groups, i);
         const SegInfo &s = segs[g];
         double x = pos[i], y = pos[n + i], z = pos[2 * n + i], m = mass[i];
-        if (!(fabs(x) <= DBL_MAX && fabs(y) <= DBL_MAX && fabs(z) <= DBL_MAX)) bad |= kBadPosition;
-        if (!(m > 0.0 && m <= DBL_MAX)) bad |= kBadMass;
+        if (!(finite_bits(x) && finite_bits(y) && finite_bits(z))) bad |= kBadPosition;
+        if (!positive_finite_bits(m)) bad |= kBadMass;
         uint32_t X = fix_open(x, s.origin[0], s.inv_q[0]);
         uint32_t Y = fix_open(y, s.origin[1], s.inv_q[1]);
         uint32_t Z = fix_open(z, s.origin[2], s.inv_q[2]);
@@ -266,19 +289,52 @@ __global__ void k_cell_table(int64_t n, const uint64_t *__restrict__ key,
                              int32_t *__restrict__ tab)
 {
     const uint64_t mmask = kl.lmax >= 21 ? 0x7fffffffffffffffull : ((1ull << (3 * kl.lmax)) - 1);
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = key[p];
-        const int g = kl.seg_bits > 0 ? (int)(k >> (3 * kl.lmax)) : 0;
-        const SegInfo &s = segs[g];
-        const int sh = 3 * (kl.lmax - s.level_c);
-        const int64_t pre = (int64_t)((k & mmask) >> sh);
-        const int64_t prev = p == s.start ? -1 : (int64_t)((key[p - 1] & mmask) >> sh);
-        int32_t *t = tab + s.tab_off;
-        for (int64_t c = prev + 1; c <= pre; c++) t[c] = (int32_t)p;
-        if (p == s.end - 1) {
-            const int64_t ncell = 1ll << (3 * s.level_c);
-            for (int64_t c = pre + 1; c <= ncell; c++) t[c] = s.end;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    // Particle p fills the cells after its predecessor's cell up to its own; the last particle
+    // of a segment also fills the cells after its own up to the end marker.  Each cell is
+    // written once.  A run of up to kOwnRun cells is written by its lane; longer runs (voids)
+    // are written by the whole warp, one run at a time, with consecutive lanes on consecutive
+    // cells.  The loop bound is the warp's first index, so the warp stays converged.
+    constexpr int64_t kOwnRun = 8;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += n_warps * 32) {
+        const int64_t p = base + lane;
+        int64_t a = 0, b = -1, a2 = 0, b2 = -1;  // runs [a, b] get p, [a2, b2] get the segment end
+        int32_t *t = tab;
+        int32_t end = 0;
+        if (p < n) {
+            const uint64_t k = key[p];
+            const int g = kl.seg_bits > 0 ? (int)(k >> (3 * kl.lmax)) : 0;
+            const SegInfo &s = segs[g];
+            const int sh = 3 * (kl.lmax - s.level_c);
+            const int64_t pre = (int64_t)((k & mmask) >> sh);
+            const int64_t prev = p == s.start ? -1 : (int64_t)((key[p - 1] & mmask) >> sh);
+            t = tab + s.tab_off;
+            a = prev + 1;
+            b = pre;
+            if (p == s.end - 1) {
+                a2 = pre + 1;
+                b2 = 1ll << (3 * s.level_c);
+                end = (int32_t)s.end;
+            }
+        }
+        const bool own1 = b - a < kOwnRun, own2 = b2 - a2 < kOwnRun;
+        if (own1)
+            for (int64_t c = a; c <= b; c++) t[c] = (int32_t)p;
+        if (own2)
+            for (int64_t c = a2; c <= b2; c++) t[c] = end;
+        for (int r = 0; r < 2; r++) {
+            unsigned m = __ballot_sync(kFull, r == 0 ? !own1 : !own2);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const int64_t ra = __shfl_sync(kFull, r == 0 ? a : a2, src);
+                const int64_t rb = __shfl_sync(kFull, r == 0 ? b : b2, src);
+                const int32_t rv = __shfl_sync(kFull, r == 0 ? (int32_t)p : end, src);
+                int32_t *rt = (int32_t *)__shfl_sync(kFull, (unsigned long long)t, src);
+                for (int64_t c = ra + lane; c <= rb; c += 32) rt[c] = rv;
+            }
         }
     }
 }
