@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -33,7 +34,7 @@ if ROOT not in sys.path:
 
 METRIC = "converged SPH particles/s (rho+h)"
 UNIT = "particles/s"
-# FP32 operations the method needs per in-h pair (definition in DESIGN.md, "Roofline"):
+# FP32 operations the method needs per in-h pair:
 # 3 differences, r^2 (3 mul + 2 add), 1 compare, 1 sqrt, q (1 mul), w (7), -q w' (5),
 # m*w (1), three sums (3) = 27, +1 for the integer count.
 FLOP_PER_PAIR = 28
@@ -119,10 +120,13 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    # the raw samples go to $SPH_BENCH_CLOCKS_DIR (default: the system temporary directory);
+    # the JSON line carries their summary
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        d = os.environ.get("SPH_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:

@@ -47,7 +47,7 @@ typedef enum {
     SPH_ERR_H_EXCEEDS_BOX = 5,  /* periodic: some h had to reach min(box)/2               */
     SPH_ERR_NOT_CONVERGED = 6,  /* max_iter passes ran out for some particles             */
     SPH_ERR_DEVICE_STATUS = 7,  /* the device flagged bad input (NaN/Inf/out-of-box)      */
-    SPH_ERR_UNSUPPORTED = 8     /* a valid option this build does not implement          */
+    SPH_ERR_UNSUPPORTED = 8     /* a valid option this library does not implement        */
 } sph_status;
 
 typedef enum { SPH_KERNEL_M4 = 0, SPH_KERNEL_WENDLAND_C6 = 1 } sph_kernel;

@@ -194,7 +194,7 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     sg.start = 0;
     sg.end = (int32_t)n;
 
-    // the segment descriptor comes from pageable host memory (staged by the driver, no
+    // the segment descriptor comes from pageable host memory (staged by the CUDA driver, no
     // allocation here); the state word must start at zero
     CUS(cudaMemcpyAsync(c.segs, &sg, sizeof(SegInfo), cudaMemcpyHostToDevice, st));
     CUS(cudaMemsetAsync(c.ds, 0, sizeof(DevState), st));
