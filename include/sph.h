@@ -135,8 +135,10 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best);
 /* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix
  * sort, gather into a sorted SoA, cell tables).  pos_xyz_dev holds three planes of n
  * doubles each (x[0..n), y[0..n), z[0..n)); mass_dev holds n doubles > 0.  Periodic
- * positions must lie in [0, box[d]).  Errors: INVALID_ARG (NULL, n < 1), OOM
- * (n > capacity), CUDA; bad positions or masses -> DEVICE_STATUS. */
+ * positions must lie in [0, box[d]) (-0.0 counts as 0); a coordinate is stored as the
+ * nearest multiple of box[d] / 2^32 (ties to even; one that rounds to box[d] wraps to 0).
+ * Masses must be finite and > 0.  Errors: INVALID_ARG (NULL, n < 1), OOM (n > capacity),
+ * CUDA; a NaN, infinite or out-of-box position or a bad mass -> DEVICE_STATUS. */
 sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const double *mass_dev);
 
 /* Solve h for the particles of the last sph_sort.  h_inout_dev: n doubles, the starting
