@@ -246,6 +246,38 @@ def test_device_flags_bad_input():
     s.close()
 
 
+def test_sort_input_edges():
+    # sph_sort's range checks: each coordinate in [0, L) with -0.0 as 0, masses finite and > 0
+    rng = np.random.default_rng(4)
+    n = 200
+    pos = rng.uniform(0, 1, (3, n))
+    mass = rng.uniform(0.5, 1.5, n)
+    pos[0, 3] = -0.0
+    pos[1, 4] = np.nextafter(1.0, 0.0)  # the largest position below the box edge
+    pos[2, 5] = 0.0
+    mass[6] = 5e-324  # subnormal, still > 0
+    h = np.full(n, 0.2)
+    g = gpu_eval(pos, mass, h, FP64)
+    o = oracle.evaluate(pos, mass, h)
+    np.testing.assert_array_equal(g["count"], o["count"])
+    np.testing.assert_allclose(g["rho"], o["rho"], rtol=1e-12)
+    s = B.Solver(n, precision=FP32)
+    for bad in (-1e-300, -np.inf, np.inf):
+        p = pos.copy()
+        p[2, 9] = bad
+        with pytest.raises(B.SphError) as e:
+            s.sort(T(p), T(mass))
+        assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    for bad in (0.0, -0.0, -1.0, np.inf, np.nan):
+        m = mass.copy()
+        m[11] = bad
+        with pytest.raises(B.SphError) as e:
+            s.sort(T(pos), T(m))
+        assert e.value.status == B.SPH_ERR_DEVICE_STATUS
+    s.sort(T(pos), T(mass))  # the valid set still sorts
+    s.close()
+
+
 def test_host_statuses_with_a_device():
     s = B.Solver(50, precision=FP32)
     h = T(np.full(50, 0.1))
