@@ -206,9 +206,111 @@ def cpu_baseline_knn(wl, n_targets, k, kernel="m4"):
             "seconds": dt}
 
 
+def cpu_baseline_batch(wl, n_groups):
+    """The oracle on a bounded sample of the c4 groups, each group solved on its own."""
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.default_rng(97)
+    pick = np.sort(rng.choice(wl.n_groups, size=min(wl.n_groups, n_groups), replace=False))
+    t0 = time.perf_counter()
+    cnt = 0
+    for gi in pick:
+        a, e = int(wl.offsets[gi]), int(wl.offsets[gi + 1])
+        oracle.solve(wl.pos[:, a:e], wl.mass[a:e], wl.h0[a:e], box=(0, 0, 0), periodic=False,
+                     nngb=float(wl.nngb[gi]), tol=float(wl.tol[gi]))
+        cnt += e - a
+    dt = time.perf_counter() - t0
+    return {"value": cnt / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{len(pick)} random groups ({cnt:,} particles) solved one after another "
+                      f"(FP64, bucket grids; a group's particles go to the threads in chunks of 16, "
+                      f"so a small group keeps few of them busy); {dt:.1f} s wall",
+            "seconds": dt, "particles": cnt}
+
+
+def run_reference_batch(args):
+    """Reference arm of the c4 batch: the oracle over a random sample of whole groups."""
+    from paper_1612_06090_gb300 import inputs
+
+    wl = inputs.make("c4")
+    n, G = wl.n, wl.n_groups
+    desc = (f"c4: {G:,} open Plummer groups (a=1, truncated at 20a), sizes dN/dN ~ N^-2 on [32, 200000], "
+            f"{n:,} particles in total, Nngb=32+-1, M4 kernel")
+    k = args.cpu_sample or 2000
+    for _ in range(args.warmup):
+        cpu_baseline_batch(wl, max(8, k // 8))
+    runs = [cpu_baseline_batch(wl, k) for _ in range(args.steps)]
+    per_step = statistics.mean(r["seconds"] for r in runs)
+    value = runs[-1]["particles"] / per_step
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "n": n, "groups": G, "sample_groups": min(k, G)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": runs[-1]["cores"], "kind": "oracle",
+                         "sample": runs[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_reference_replay(args):
+    """Reference arm of the c5 replay: sampled targets of snapshot 1, warm-started from their
+    snapshot-0 solution (which is solved first, untimed), brute force over all particles."""
+    import numpy as np
+
+    import oracle
+    from paper_1612_06090_gb300 import inputs
+
+    kw = {"n": args.n} if args.n else {}
+    series = inputs.clumpy_snapshot_series(2, **kw)
+    wl0 = next(series)
+    wl1 = next(series)
+    n = wl0.n
+    desc = (f"c5: {n:,} particles, 4096 Plummer clumps (a log-uniform in [1e-3,1e-2], 70%) + background, "
+            f"periodic unit box, Nngb=64+-2; 8 snapshots drifting N(0,1e-4^2), warm-started replay")
+    # the oracle hands targets to its threads in chunks of 16: 16 per thread keeps all busy
+    k = min(args.cpu_sample or 16 * oracle.threads(), n)
+    tg = np.sort(np.random.default_rng(96).choice(n, size=k, replace=False))
+    cold = oracle.solve(wl0.pos, wl0.mass, wl0.h0[tg], nngb=wl0.nngb, tol=wl0.tol, targets=tg, mode="brute")
+
+    def warm(t):
+        t0 = time.perf_counter()
+        r = oracle.solve(wl1.pos, wl1.mass, cold["h"][t], nngb=wl1.nngb, tol=wl1.tol, targets=tg[t],
+                         mode="brute")
+        return time.perf_counter() - t0, r
+
+    for _ in range(args.warmup):
+        warm(np.arange(min(16, k)))
+    times = []
+    for _ in range(args.steps):
+        dt, r = warm(np.arange(k))
+        times.append(dt)
+    per_step = statistics.mean(times)
+    value = k / per_step
+    sample = (f"{k} random targets of snapshot 1, warm-started from their snapshot-0 solution, each "
+              f"solved by brute force against all {n:,} particles (FP64, OpenMP over targets); "
+              f"{r['stats']['passes']} passes, {per_step:.1f} s wall")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "n": n, "sample_targets": k},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(oracle.threads(), -(-k // 16)),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args):
     rank, world = dist_init(args)
     if rank != 0:
+        return
+    if not args.knn and args.config in ("c4", "c5"):
+        line = run_reference_batch(args) if args.config == "c4" else run_reference_replay(args)
+        line["n_gpus"] = world
+        print(json.dumps(line), flush=True)
         return
     wl, desc = workload(args)
     if args.knn:

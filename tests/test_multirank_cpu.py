@@ -68,3 +68,34 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
                               kernel="m4")
     bench.run_reference(args)
     assert capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("config,n,knn,sample", [("c2", 16384, 0, 256), ("c4", 0, 0, 40),
+                                                 ("c5", 65536, 0, 32), ("c2", 16384, 16, 64)])
+def test_reference_arm_json_line(monkeypatch, capsys, config, n, knn, sample):
+    """The reference arm (the oracle on a bounded sample) prints one line with the keys of the
+    bench contract, its own value repeated as cpu_baseline and e2e, and no host copies."""
+    import argparse
+    import json
+
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = argparse.Namespace(impl="reference", config=config, n=n, steps=2, warmup=1,
+                              cpu_sample=sample, kernel="m4", knn=knn)
+    bench.run_reference(args)
+    lines = [x for x in capsys.readouterr().out.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["metric"] == (bench.KNN_METRIC if knn else bench.METRIC) and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"].startswith(config + ":")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
