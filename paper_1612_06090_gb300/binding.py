@@ -263,6 +263,26 @@ class SphError(RuntimeError):
         self.status = status
 
 
+def check_tensor(t, name: str, dtype, shape=None, device=None, ndim=None, cuda=True):
+    """Reject a tensor the library would misread: it receives bare device pointers and reads
+    or writes exactly the documented number of elements of the documented type, so a wrong
+    dtype, size or device would be read past its end, overrun or dereferenced on the wrong GPU.
+    Checked in this order: a tensor, dtype, number of dimensions, shape, then (cuda=True) the
+    CUDA device.  Raises TypeError (not a tensor, wrong dtype) or ValueError (the rest)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimension(s), got shape {tuple(t.shape)}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if cuda and (t.device.type != "cuda" or (device is not None and t.device.index != device)):
+        raise ValueError(f"{name} must be on the context's CUDA device cuda:{device}, got {t.device}")
+
+
 class Solver:
     """One context on the current CUDA device and stream, driven with torch tensors.
 
@@ -283,7 +303,8 @@ class Solver:
         if st != SPH_OK:
             raise SphError(st, "sph_create failed")
         self.ctx = ctx
-        self.n = 0
+        self.device = torch.cuda.current_device()
+        self.n = 0  # particles of the last successful sph_sort (0: none)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -301,6 +322,12 @@ class Solver:
             raise SphError(st, sph_last_error(self.ctx))
         return st
 
+    def _per_particle(self, t, name, dtype=None, cuda=True):
+        """A per-particle array of the sorted set.  Before any sort the length is not checked:
+        the library then answers NOT_SORTED without touching the arrays."""
+        dtype = dtype if dtype is not None else self._torch.float64
+        check_tensor(t, name, dtype, (self.n,) if self.n > 0 else None, self.device, ndim=1, cuda=cuda)
+
     def tuning(self) -> dict:
         st, t = sph_get_tuning(self.ctx)
         self._check(st)
@@ -314,7 +341,8 @@ class Solver:
         self._check(sph_set_tuning(self.ctx, t))
 
     def autotune(self, h0) -> dict:
-        st, t = sph_autotune(self.ctx, h0.data_ptr())
+        self._per_particle(h0, "h0")
+        st, t = sph_autotune(self.ctx, h0.contiguous().data_ptr())
         self._check(st)
         return t.to_dict()
 
@@ -323,17 +351,36 @@ class Solver:
         self._check(sph_set_params(self.ctx, self.params))
 
     def sort(self, pos, mass):
+        torch = self._torch
+        check_tensor(mass, "mass", torch.float64, ndim=1, cuda=False)
+        n = int(mass.shape[0])
+        check_tensor(pos, "pos", torch.float64, (3, n), cuda=False)
+        for t, name in ((pos, "pos"), (mass, "mass")):
+            check_tensor(t, name, t.dtype, device=self.device)
         pos = pos.contiguous()
         mass = mass.contiguous()
         self._pos, self._mass = pos, mass  # keep alive until the stream has used them
-        self.n = int(mass.shape[0])
-        self._check(sph_sort(self.ctx, self.n, pos.data_ptr(), mass.data_ptr()))
+        self.n = 0
+        self._check(sph_sort(self.ctx, n, pos.data_ptr(), mass.data_ptr()))
+        self.n = n
 
     def solve(self, h0, out=None):
         torch = self._torch
-        h = h0.clone() if out is None else out["h"].copy_(h0)
+        checks = [(h0, "h0", torch.float64)]
+        if out is not None:
+            checks += [(out[k], f"out['{k}']", dt) for k, dt in (("h", torch.float64), ("rho", torch.float64),
+                                                                  ("count", torch.int32), ("nw", torch.float64))]
+        for t, name, dt in checks:
+            self._per_particle(t, name, dt, cuda=False)
+        for t, name, dt in checks:
+            self._per_particle(t, name, dt)
+        if out is not None:
+            for k in ("h", "rho", "count", "nw"):
+                if not out[k].is_contiguous():
+                    raise ValueError(f"out['{k}'] must be contiguous")
+        h = h0.clone(memory_format=torch.contiguous_format) if out is None else out["h"].copy_(h0)
         rho = torch.empty_like(h) if out is None else out["rho"]
-        count = torch.empty(self.n, dtype=torch.int32, device=h.device) if out is None else out["count"]
+        count = torch.empty(h.shape[0], dtype=torch.int32, device=h.device) if out is None else out["count"]
         nw = torch.empty_like(h) if out is None else out["nw"]
         stats = SphStats()
         st = self._check(sph_density_solve(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
@@ -345,10 +392,11 @@ class Solver:
         """k-nearest-neighbour h (distance to the k-th nearest particle) and rho there; h0 is
         the starting search radius per particle."""
         torch = self._torch
-        h = h0.clone()
+        self._per_particle(h0, "h0")
+        h = h0.clone(memory_format=torch.contiguous_format)
         rho = torch.empty_like(h)
         nw = torch.empty_like(h)
-        count = torch.empty(self.n, dtype=torch.int32, device=h.device)
+        count = torch.empty(h.shape[0], dtype=torch.int32, device=h.device)
         stats = SphStats()
         st = self._check(sph_knn_solve(self.ctx, int(k), h.data_ptr(), rho.data_ptr(), count.data_ptr(),
                                        nw.data_ptr(), stats),
@@ -357,23 +405,36 @@ class Solver:
 
     def evaluate(self, h):
         torch = self._torch
+        self._per_particle(h, "h")
+        h = h.contiguous()
         rho = torch.empty_like(h)
         nw = torch.empty_like(h)
         dnw = torch.empty_like(h)
-        count = torch.empty(self.n, dtype=torch.int32, device=h.device)
+        count = torch.empty(h.shape[0], dtype=torch.int32, device=h.device)
         self._check(sph_density_eval(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
                                      nw.data_ptr(), dnw.data_ptr()))
         return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
 
     def batch_solve(self, offsets, pos, mass, h0, nngb, tol):
         torch = self._torch
+        check_tensor(offsets, "offsets", torch.int64, ndim=1, cuda=False)
+        check_tensor(mass, "mass", torch.float64, ndim=1, cuda=False)
+        n_all, g_all = int(mass.shape[0]), max(int(offsets.shape[0]) - 1, 0)
+        check_tensor(pos, "pos", torch.float64, (3, n_all), cuda=False)
+        check_tensor(h0, "h0", torch.float64, (n_all,), cuda=False)
+        check_tensor(nngb, "nngb", torch.float64, (g_all,), cuda=False)
+        check_tensor(tol, "tol", torch.float64, (g_all,), cuda=False)
+        for t, name in ((offsets, "offsets"), (pos, "pos"), (mass, "mass"), (h0, "h0"), (nngb, "nngb"),
+                        (tol, "tol")):
+            check_tensor(t, name, t.dtype, device=self.device)
+        self.n = 0  # the context now holds groups, not one sorted set
         offsets = offsets.contiguous()
         pos = pos.contiguous()
         mass = mass.contiguous()
         nngb = nngb.contiguous()
         tol = tol.contiguous()
         n = int(mass.shape[0])
-        h = h0.clone()
+        h = h0.clone(memory_format=torch.contiguous_format)
         rho = torch.empty_like(h)
         nw = torch.empty_like(h)
         count = torch.empty(n, dtype=torch.int32, device=h.device)

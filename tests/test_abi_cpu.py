@@ -119,3 +119,50 @@ def test_without_a_gpu_create_reports_cuda(B):
     st, ctx = B.sph_create(B.make_params(), 1000)
     assert st == B.SPH_ERR_CUDA
     assert ctx is None
+
+
+def test_binding_rejects_tensors_the_library_would_misread(B):
+    """The Solver wrapper checks dtype, dimensions, length and device before passing a bare
+    pointer: a float32 h would be read past its end and its outputs overrun."""
+    torch = pytest.importorskip("torch")
+    f64, f32, i64 = torch.float64, torch.float32, torch.int64
+    n = 8
+    with pytest.raises(TypeError):
+        B.check_tensor([1.0], "x", f64)
+    with pytest.raises(TypeError):
+        B.check_tensor(torch.zeros(n, dtype=f32), "x", f64)
+    with pytest.raises(ValueError, match="dimension"):
+        B.check_tensor(torch.zeros(2, n, dtype=f64), "x", f64, ndim=1)
+    with pytest.raises(ValueError, match="shape"):
+        B.check_tensor(torch.zeros(n + 1, dtype=f64), "x", f64, (n,))
+    with pytest.raises(ValueError, match="CUDA"):
+        B.check_tensor(torch.zeros(n, dtype=f64), "x", f64, (n,))  # a CPU tensor
+
+    s = B.Solver.__new__(B.Solver)  # no context: every check must fire before the library
+    s._torch, s.ctx, s.device, s.n = torch, None, 0, n
+    cases = [
+        (lambda: s.sort(torch.zeros(3, n, dtype=f32), torch.ones(n, dtype=f64)), TypeError),
+        (lambda: s.sort(torch.zeros(n, 3, dtype=f64), torch.ones(n, dtype=f64)), ValueError),
+        (lambda: s.sort(torch.zeros(3, n, dtype=f64), torch.ones(n, 1, dtype=f64)), ValueError),
+        (lambda: s.sort(torch.zeros(3, n, dtype=f64), torch.ones(n, dtype=f64)), ValueError),  # CPU
+        (lambda: s.solve(torch.ones(n, dtype=f32)), TypeError),
+        (lambda: s.solve(torch.ones(n - 1, dtype=f64)), ValueError),
+        (lambda: s.evaluate(torch.ones(n, dtype=f32)), TypeError),
+        (lambda: s.evaluate(torch.ones(n + 1, dtype=f64)), ValueError),
+        (lambda: s.knn(4, torch.ones(n, dtype=f32)), TypeError),
+        (lambda: s.knn(4, torch.ones(2, n, dtype=f64)), ValueError),
+        (lambda: s.autotune(torch.ones(n, dtype=f32)), TypeError),
+        (lambda: s.batch_solve(torch.tensor([0, n], dtype=torch.int32), torch.zeros(3, n, dtype=f64),
+                               torch.ones(n, dtype=f64), torch.ones(n, dtype=f64),
+                               torch.ones(1, dtype=f64), torch.ones(1, dtype=f64)), TypeError),
+        (lambda: s.batch_solve(torch.tensor([0, n], dtype=i64), torch.zeros(3, n, dtype=f64),
+                               torch.ones(n, dtype=f64), torch.ones(n, dtype=f64),
+                               torch.ones(2, dtype=f64), torch.ones(1, dtype=f64)), ValueError),
+    ]
+    for call, err in cases:
+        with pytest.raises(err):
+            call()
+    out = {"h": torch.ones(n, dtype=f64), "rho": torch.ones(n, dtype=f64), "count": torch.ones(n, dtype=f64),
+           "nw": torch.ones(n, dtype=f64)}
+    with pytest.raises(TypeError, match="count"):  # counts are int32
+        s.solve(torch.ones(n, dtype=f64), out=out)
