@@ -112,6 +112,10 @@ typedef struct {
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
  * on the current CUDA device, with scratch for up to `capacity` particles (and up to
  * `capacity` batch groups).  Allocates all device memory the context will ever use.
+ * The parameters are the paper's statement of the problem (Sec. II-B with Eq. 1): the
+ * kernel (Wendland C6 in the paper, M4 by default here), the target neighbour number
+ * (295 in the paper) with its tolerance, the periodic box, and the recompute limit of
+ * Sec. IV-A.
  * Errors: INVALID_ARG (NULL params/out, capacity < 1 or > 2^31 - 2^20, bad params),
  * CUDA (no device), OOM (device allocation failed). */
 sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_stream, sph_ctx **out);
@@ -124,7 +128,8 @@ sph_status sph_set_params(sph_ctx *ctx, const sph_params *params);
 sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
 sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
 
-/* Autotuner: time the grouping level (group_shift -1..1) and the candidate cell size
+/* Autotuner: the GPU counterpart of the work distribution choices of Sec. IV-A (dynamic
+ * scheduling of uneven per-particle work).  Time the grouping level (group_shift -1..1) and the candidate cell size
  * (cell_div 2..3) with full solves from h_dev (n doubles, caller order, read only) on the
  * particles of the last sph_sort, keep the fastest in the context and, when the context has
  * a tune_cache file, append it there; sph_sort applies the last cached entry that matches
@@ -133,7 +138,10 @@ sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
 sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best);
 
 /* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix
- * sort, gather into a sorted SoA, cell tables).  pos_xyz_dev holds three planes of n
+ * sort, gather into a sorted SoA, cell tables).  This is the spatial structure behind the
+ * neighbour search: the paper's Barnes-Hut tree stored as a flat array (Sec. II-A), here an
+ * octree implicit in the Morton order, and its AoS-to-SoA gather (Sec. IV-B).  The gather
+ * keeps only the fields the density loop reads.  pos_xyz_dev holds three planes of n
  * doubles each (x[0..n), y[0..n), z[0..n)); mass_dev holds n doubles > 0.  Periodic
  * positions must lie in [0, box[d]) (-0.0 counts as 0); a coordinate is stored as the
  * nearest multiple of box[d] / 2^32 (ties to even; one that rounds to box[d] wraps to 0).
@@ -141,7 +149,9 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best);
  * CUDA; a NaN, infinite or out-of-box position or a bad mass -> DEVICE_STATUS. */
 sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const double *mass_dev);
 
-/* Solve h for the particles of the last sph_sort.  h_inout_dev: n doubles, the starting
+/* Solve h for the particles of the last sph_sort: the recompute loop of Sec. IV-A
+ * (Listing 3), each pass evaluating Eq. (1) for the particles on the todo list and
+ * adjusting the h of those still outside the band.  h_inout_dev: n doubles, the starting
  * h on entry (0 < h < min(box)/2 when periodic) and the final h on exit; rho_out_dev:
  * n doubles; count_out_dev: n int32 (integer neighbour count, self included);
  * nw_out_dev: n doubles or NULL (weighted count N_w).  An unconverged particle gets the
@@ -152,10 +162,33 @@ sph_status sph_density_solve(sph_ctx *ctx, double *h_inout_dev, double *rho_out_
                              int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats);
 
 /* One density evaluation at fixed h (no iteration) for the particles of the last
- * sph_sort.  h_dev: n doubles in caller order.  Outputs (caller order): rho, integer
+ * sph_sort: Eq. (1) in gather form, the density loop of Listing 1 over every particle.
+ * h_dev: n doubles in caller order.  Outputs (caller order): rho, integer
  * count, N_w and dN_w/dh; nw/dnw may be NULL. */
 sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_dev,
                             int32_t *count_out_dev, double *nw_out_dev, double *dnw_out_dev);
+
+/* Neighbour sets of sampled particles, for checking the search itself (a test aid).
+ * Listing 1 loops over a neighbour list (ngblist) of the particles within h; the GPU never
+ * stores such lists, it tests staged candidates against h on the fly.  This call runs one
+ * density evaluation at fixed h exactly as sph_density_eval does (the same work items,
+ * staging, FP32 or FP64 distance tests and kernel instantiation apart from the recording)
+ * and, for each sampled particle, records every particle j with r_ij < h_i (the particle
+ * itself included), i.e. the neighbour list Eq. (1) sums over.
+ *   h_dev:          n doubles, caller order (as sph_density_eval);
+ *   sample_dev:     n_sample distinct caller indices in [0, n), 1 <= n_sample <= n (int64);
+ *   nbr_dev:        n_sample * max_nbr int32; row k receives the caller indices of the
+ *                   neighbours of sample k, in no particular order;
+ *   nbr_count_dev:  n_sample int32: the number of neighbours of sample k (all of them, also
+ *                   when more than max_nbr exist; only the first max_nbr are written);
+ *   rho_out_dev, count_out_dev: n entries each, as sph_density_eval (count_out[sample[k]]
+ *                   equals nbr_count[k]).
+ * Uses context scratch only.  Errors: INVALID_ARG (NULL, n_sample outside [1, n],
+ * max_nbr < 1, a sample index outside [0, n) or repeated), NOT_SORTED, UNSUPPORTED (FP32
+ * with direct_pct != 0), DEVICE_STATUS (bad h), CUDA. */
+sph_status sph_neighbours_sampled(sph_ctx *ctx, const double *h_dev, int64_t n_sample,
+                                  const int64_t *sample_dev, int32_t max_nbr, int32_t *nbr_dev,
+                                  int32_t *nbr_count_dev, double *rho_out_dev, int32_t *count_out_dev);
 
 /* k-nearest-neighbour smoothing lengths: the Subfind form of the density loop (Sec. IV-D and
  * Listing 3), where each particle's neighbour list is put in order of distance and its K
@@ -185,7 +218,9 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
 sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *rho_out_dev,
                          int32_t *count_out_dev, double *nw_out_dev, sph_stats *stats);
 
-/* Solve many independent non-periodic groups in one pass loop.  Group g owns the
+/* Solve many independent non-periodic groups in one pass loop: the recompute loop of
+ * Sec. IV-A (Listing 3) with Eq. (1), run over many independent particle sets at once, each
+ * with its own neighbour target and tolerance (Sec. II-B).  Group g owns the
  * particles [offsets[g], offsets[g+1]) of the flattened arrays; offsets_dev holds
  * n_groups + 1 int64 (offsets[0] = 0, non-decreasing); nngb_dev and tol_dev hold one
  * double per group.  pos_xyz_dev is three planes of n = offsets[n_groups] doubles.

@@ -34,7 +34,8 @@ SPH_MAX_PASSES = 64
 EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sph_density_eval",
             "sph_knn_solve",
             "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error",
-            "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning", "sph_autotune")
+            "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning", "sph_autotune",
+            "sph_neighbours_sampled")
 SPH_STATIC_MAX_PARTICLES = 32768
 SPH_KNN_MAX_K = 512
 
@@ -142,6 +143,8 @@ def lib() -> ctypes.CDLL:
     L.sph_set_tuning.argtypes = [vp, ctypes.POINTER(SphTuning)]
     L.sph_autotune.restype = i32
     L.sph_autotune.argtypes = [vp, vp, ctypes.POINTER(SphTuning)]
+    L.sph_neighbours_sampled.restype = i32
+    L.sph_neighbours_sampled.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, vp]
     L.sph_density_eval_static.restype = i32
     L.sph_density_eval_static.argtypes = [ctypes.POINTER(SphParams), i64, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = L
@@ -218,6 +221,14 @@ def sph_density_eval(ctx, h_ptr: int, rho_ptr: int, count_ptr: int, nw_ptr: int 
     return lib().sph_density_eval(ctypes.c_void_p(ctx), ctypes.c_void_p(h_ptr or None),
                                   ctypes.c_void_p(rho_ptr or None), ctypes.c_void_p(count_ptr or None),
                                   ctypes.c_void_p(nw_ptr or None), ctypes.c_void_p(dnw_ptr or None))
+
+
+def sph_neighbours_sampled(ctx, h_ptr: int, n_sample: int, sample_ptr: int, max_nbr: int, nbr_ptr: int,
+                           nbr_count_ptr: int, rho_ptr: int, count_ptr: int) -> int:
+    v = lambda p: ctypes.c_void_p(p or None)  # noqa: E731
+    return lib().sph_neighbours_sampled(ctypes.c_void_p(ctx), v(h_ptr), int(n_sample), v(sample_ptr),
+                                        int(max_nbr), v(nbr_ptr), v(nbr_count_ptr), v(rho_ptr),
+                                        v(count_ptr))
 
 
 def sph_batch_solve(ctx, n_groups: int, offsets_ptr: int, pos_xyz_ptr: int, mass_ptr: int,
@@ -414,6 +425,26 @@ class Solver:
         self._check(sph_density_eval(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
                                      nw.data_ptr(), dnw.data_ptr()))
         return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
+
+    def neighbours(self, h, sample, max_nbr):
+        """Neighbour sets of the sampled particles at fixed h (one density evaluation that also
+        records them).  sample: int64 caller indices.  Returns nbr (n_sample, max_nbr) int32
+        (row k: caller indices of sample k's neighbours, first nbr_count[k] entries valid, at
+        most max_nbr), nbr_count (n_sample,) int32, and rho/count of every particle."""
+        torch = self._torch
+        self._per_particle(h, "h")
+        check_tensor(sample, "sample", torch.int64, ndim=1, device=self.device)
+        h = h.contiguous()
+        sample = sample.contiguous()
+        ns = int(sample.shape[0])
+        nbr = torch.empty((ns, int(max_nbr)), dtype=torch.int32, device=h.device)
+        nbr_count = torch.empty(ns, dtype=torch.int32, device=h.device)
+        rho = torch.empty_like(h)
+        count = torch.empty(h.shape[0], dtype=torch.int32, device=h.device)
+        self._check(sph_neighbours_sampled(self.ctx, h.data_ptr(), ns, sample.data_ptr(), int(max_nbr),
+                                           nbr.data_ptr(), nbr_count.data_ptr(), rho.data_ptr(),
+                                           count.data_ptr()))
+        return {"nbr": nbr, "nbr_count": nbr_count, "rho": rho, "count": count}
 
     def batch_solve(self, offsets, pos, mass, h0, nngb, tol):
         torch = self._torch

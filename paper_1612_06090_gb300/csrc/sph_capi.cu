@@ -47,6 +47,7 @@ struct sph_ctx {
            *e_nw = nullptr, *e_dnw = nullptr;
     int32_t *e_cnt = nullptr, *todo[2] = {nullptr, nullptr}, *flags = nullptr, *items = nullptr;
     int32_t *tsize = nullptr, *toff = nullptr;
+    int32_t *nb_slot = nullptr;  // neighbour export: caller index -> sample row
     float *h32 = nullptr, *e_rho32 = nullptr, *e_nw32 = nullptr, *e_dnw32 = nullptr;
     DevState *ds = nullptr;
 
@@ -172,6 +173,7 @@ size_t carve(sph_ctx *c, char *base)
     c->e_dnw32 = (float *)take(cap * 4);
     c->tsize = (int32_t *)take((gcap + 1) * 4);
     c->toff = (int32_t *)take((gcap + 1) * 4);
+    c->nb_slot = (int32_t *)take(cap * 4);
     c->ds = (DevState *)take(sizeof(DevState));
     return off;
 }
@@ -314,6 +316,7 @@ sph_status device_status_error(sph_ctx *c, int bits)
     if (bits & kBadMass) what += " non-positive or non-finite mass;";
     if (bits & kBadH) what += " h not in (0, min(box)/2) or bad group nngb/tol;";
     if (bits & 8) what += " internal cell-count guard;";
+    if (bits & kBadSample) what += " sample index outside [0, n) or repeated;";
     return fail(c, SPH_ERR_DEVICE_STATUS, "device flagged the input:%s", what.c_str());
 }
 
@@ -762,6 +765,45 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
         return device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
     CU(ctx, launch_pass(a, 0, false, st), "density pass");
     CU(ctx, launch_scatter(a, nullptr, rho_out_dev, count_out_dev, nw_out_dev, dnw_out_dev, st), "scatter");
+    s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    return SPH_OK;
+}
+
+sph_status sph_neighbours_sampled(sph_ctx *ctx, const double *h_dev, int64_t n_sample,
+                                  const int64_t *sample_dev, int32_t max_nbr, int32_t *nbr_dev,
+                                  int32_t *nbr_count_dev, double *rho_out_dev, int32_t *count_out_dev)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!h_dev || !sample_dev || !nbr_dev || !nbr_count_dev || !rho_out_dev || !count_out_dev)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
+    if (n_sample < 1 || n_sample > ctx->n)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "n_sample = %lld outside [1, n = %lld]", (long long)n_sample,
+                    (long long)ctx->n);
+    if (max_nbr < 1) return fail(ctx, SPH_ERR_INVALID_ARG, "max_nbr must be >= 1");
+    if (ctx->params.precision != SPH_PREC_FP64 && ctx->tuning.direct_pct != 0)
+        return fail(ctx, SPH_ERR_UNSUPPORTED, "the neighbour export needs direct_pct = 0 in FP32");
+    cudaStream_t st = ctx->stream;
+    SolveArgs a = solve_args(ctx);
+    CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+    CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
+    CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
+    CU(ctx, launch_nb_setup(a, ctx->nb_slot, sample_dev, n_sample, nbr_count_dev, st), "sample set-up");
+    sph_status s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    {
+        const int bits = ctx->ds_host->status | ctx->ds_host->sort_status;
+        if (bits & kBadSample) return fail(ctx, SPH_ERR_INVALID_ARG, "a sample index is outside [0, n) or repeated");
+        if (bits) return device_status_error(ctx, bits);
+    }
+    a.nb_slot = ctx->nb_slot;
+    a.nb_out = nbr_dev;
+    a.nb_cnt = nbr_count_dev;
+    a.nb_max = max_nbr;
+    CU(ctx, launch_pass(a, 0, false, st), "density pass with the neighbour export");
+    CU(ctx, launch_scatter(a, nullptr, rho_out_dev, count_out_dev, nullptr, nullptr, st), "scatter");
     s = read_state(ctx);
     if (s != SPH_OK) return s;
     if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);

@@ -75,6 +75,7 @@ enum DevStatusBits : int32_t {
     kBadPosition = 1,   // NaN/Inf coordinate, or outside [0, box) when periodic
     kBadMass = 2,       // mass not finite or <= 0
     kBadH = 4,          // h not finite, <= 0, or >= min(box)/2 when periodic
+    kBadSample = 16,    // neighbour export: a sample index outside [0, n) or repeated
 };
 
 // ---------------------------------------------------------------------------------------

@@ -174,7 +174,7 @@ struct Acc64 {
 };
 
 template <int kKern>
-__device__ __forceinline__ void pair64(const double4_32a &ti, const double4_32a &cj, double h,
+__device__ __forceinline__ bool pair64(const double4_32a &ti, const double4_32a &cj, double h,
                                        double h2, const SegInfo &S, Acc64 &A)
 {
     double dx = __dsub_rn(cj.x, ti.x);
@@ -193,7 +193,16 @@ __device__ __forceinline__ void pair64(const double4_32a &ti, const double4_32a 
         A.s_w = __dadd_rn(A.s_w, w);
         A.s_dw = __dadd_rn(A.s_dw, kKern == 0 ? mqdw64(q) : mqdw64_c6(q));
         A.count++;
+        return true;
     }
+    return false;
+}
+
+// Neighbour export: one in-h pair of a sampled target (sorted position j of the neighbour).
+__device__ __forceinline__ void nb_record(const SolveArgs &a, int slot, int j)
+{
+    const int c = atomicAdd(&a.nb_cnt[slot], 1);
+    if (c < a.nb_max) a.nb_out[(int64_t)slot * a.nb_max + c] = a.idx[j];
 }
 
 // Per-lane geometry of the pair loop: lane = (target t, slice s); the lane tests staged
@@ -204,6 +213,7 @@ struct LaneTarget {
     float hinv2;
     int slices, s;
     int sh;            // log2(slices)
+    int slot;          // neighbour export: sample row of the target, or -1
 };
 
 // Stage layout of the packed FP32 path (kMode 2).  Candidate slot j is tested by slice
@@ -255,13 +265,15 @@ __device__ __forceinline__ void shape32x2(float2 q, float2 &w, float2 &dw)
 // in-h pairs fall across the targets.
 // kMode: 0 = FP64 (queue), 1 = FP32 with the queue until the in-h share is known, 2 = FP32
 // evaluated directly (no queue, no ring memory).
-template <int kMode, int kKern>
+// kExp: also record the in-h candidates of sampled targets (neighbour export; sidx then holds
+// every staged candidate's sorted position in linear slot order).
+template <int kMode, int kKern, bool kExp>
 __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__restrict__ sidx,
                                       void *__restrict__ ring_raw, int cnt, int direct_pct,
                                       const LaneTarget &L,
                                       Acc32 &A32, Acc64 &A64, const double4_32a &ti, double h,
                                       double h2, const SegInfo &S,
-                                      const double4_32a *__restrict__ pdbl)
+                                      const double4_32a *__restrict__ pdbl, const SolveArgs &a)
 {
     constexpr bool kF64 = kMode == 0;
     constexpr bool kQueue = kMode < 2;
@@ -288,6 +300,14 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
                 const float2 dz = __fadd2_rn(f2(B.x, B.y), ntz);
                 const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
                 const bool in0 = r2.x < L.h2, in1 = r2.y < L.h2;
+                if constexpr (kExp) {
+                    if (L.slot >= 0) {
+                        // slots of steps 2i and 2i + 1 of this lane's slice
+                        const int j0 = ((2 * i) << L.sh) + L.s, j1 = j0 + (1 << L.sh);
+                        if (in0 && j0 < cnt) nb_record(a, L.slot, sidx[j0]);
+                        if (in1 && j1 < cnt) nb_record(a, L.slot, sidx[j1]);
+                    }
+                }
                 // kMode 2: the pair body runs when either candidate is within h, so a step in
                 // which no lane has one costs only the test; kMode 3: branch-free, the
                 // unrolled bodies interleave (candidates outside h add exactly zero)
@@ -321,7 +341,8 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
     auto drain_one = [&](int &head) {
         if (kF64) {
             const int j = ring64[head & (kRing - 1)][lane];
-            pair64<kKern>(ti, pdbl[sidx[j]], h, h2, S, A64);
+            const bool in = pair64<kKern>(ti, pdbl[sidx[j]], h, h2, S, A64);
+            if (kExp && in && L.slot >= 0) nb_record(a, L.slot, sidx[j]);
         } else {
             pair32<kKern>(ring32[head & (kRing - 1)][lane], L.hinv2, A32);
         }
@@ -396,30 +417,34 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
 
 // Per-warp shared memory: the stage, the mode's queue memory, then the item's cell table
 // (exclusive prefix of the cell sizes and first particle of every cell).
-template <int kMode>
+// The neighbour export (kExp) adds the staged candidates' sorted positions to the FP32 modes.
+template <int kMode, bool kExp = false>
 __host__ __device__ constexpr int warp_cell_offset()
 {
-    return kStageCap * 16 + (kMode == 0 ? kStageCap * 4 + kRing * 32 * 4 : kMode == 1 ? kRing * 32 * 8 : 0);
+    return kStageCap * 16 + (kMode == 0   ? kStageCap * 4 + kRing * 32 * 4
+                             : kMode == 1 ? kRing * 32 * 8
+                             : kExp       ? kStageCap * 4
+                                          : 0);
 }
 
-template <int kMode>
+template <int kMode, bool kExp = false>
 __host__ __device__ constexpr int warp_smem_bytes()
 {
-    return warp_cell_offset<kMode>() + 2 * kMaxCells * 4;
+    return warp_cell_offset<kMode, kExp>() + 2 * kMaxCells * 4;
 }
 
-template <int kMode, int kKern>
+template <int kMode, int kKern, bool kExp = false>
 __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
     k_density(SolveArgs a, const int32_t *__restrict__ todo)
 {
     constexpr bool kF64 = kMode == 0;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wbase = smem + (size_t)warp * warp_smem_bytes<kMode>();
+    unsigned char *wbase = smem + (size_t)warp * warp_smem_bytes<kMode, kExp>();
     float4 *stage = (float4 *)wbase;
     int *sidx = (int *)(wbase + kStageCap * 16);
     void *ring = wbase + kStageCap * 16 + (kF64 ? kStageCap * 4 : 0);
-    int *cpre = (int *)(wbase + warp_cell_offset<kMode>());
+    int *cpre = (int *)(wbase + warp_cell_offset<kMode, kExp>());
     int *cbeg = cpre + kMaxCells;
     // the branched (2) and branch-free (3) FP32 kernels are both launched when the pass may use
     // either; the one the pass did not choose returns at once
@@ -446,6 +471,7 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         L.s = lane / Gp;
         const bool active = t < G;
         const int p = todo[t0 + (active ? t : 0)];
+        L.slot = kExp && active ? a.nb_slot[a.idx[p]] : -1;
         const uint4 P = a.pfix[p];
         const double hd = kF64 ? a.h[p] : 0.0;
         const float hf = kF64 ? (float)hd : a.h32[p];
@@ -456,6 +482,41 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         int rel[3];
         item_setup(S, a.kl, a.cell_div, active, P, hf, G3, rel);
         const float qf[3] = {(float)S.q[0], (float)S.q[1], (float)S.q[2]};
+        // FP32 offsets are taken from the centre of the targets' box rather than the first
+        // target: the largest offset a near-boundary pair needs is then half the box plus h,
+        // which bounds the rounding of the FP32 distance test.  The origin moves to the centre
+        // (X0 + cen) once per item, with the query bounds; the ball centre and the cells are
+        // found relative to the first target before the move.
+        float ccx, ccy, ccz, ball2;
+        const float cc0[3] = {0.5f * ((float)G3.bmin[0] + (float)G3.bmax[0]) * qf[0],
+                              0.5f * ((float)G3.bmin[1] + (float)G3.bmax[1]) * qf[1],
+                              0.5f * ((float)G3.bmin[2] + (float)G3.bmax[2]) * qf[2]};
+        {
+            const float qm = fmaxf(qf[0], fmaxf(qf[1], qf[2]));
+            float half2 = 0.f, c2[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const float hx = 0.5f * (float)((int64_t)G3.bmax[d] - (int64_t)G3.bmin[d]) * qf[d];
+                half2 = fmaf(hx, hx, half2);
+                const int64_t sum = (int64_t)G3.bmin[d] + (int64_t)G3.bmax[d];
+                const int64_t cen = sum >> 1;
+                c2[d] = 0.5f * (float)(sum - 2 * cen) * qf[d];  // 0 or half a unit
+                // the wrapped 32-bit differences from the new origin are exact: the true
+                // offset of any candidate within h of a target of this item fits in 32 bits
+                G3.X0[d] += (uint32_t)cen;
+                rel[d] = (int32_t)((uint32_t)rel[d] - (uint32_t)cen);
+                if (!G3.full[d]) {
+                    const int64_t lo = G3.lo[d] - cen, hi = G3.hi[d] - cen;
+                    G3.qlo[d] = (int)(lo < INT_MIN ? (int64_t)INT_MIN : lo);
+                    G3.qhi[d] = (int)(hi > INT_MAX ? (int64_t)INT_MAX : hi);
+                }
+            }
+            ccx = c2[0];
+            ccy = c2[1];
+            ccz = c2[2];
+            const float Rm = (sqrtf(half2) + G3.hmax) * (1.0f + 1e-5f) + 8.0f * qm;
+            ball2 = Rm * Rm;
+        }
         L.tx = (float)rel[0] * qf[0];
         L.ty = (float)rel[1] * qf[1];
         L.tz = (float)rel[2] * qf[2];
@@ -481,26 +542,8 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         // centre of the targets' box of radius (half-diagonal + h_max); staging keeps the
         // box test (exact, integer) and adds this ball test (FP32 with a margin that covers
         // the rounding of the offsets and the fixed-point quantisation).
-        float ccx, ccy, ccz, ball2;
-        {
-            const float qm = fmaxf(qf[0], fmaxf(qf[1], qf[2]));
-            float half2 = 0.f;
-            for (int d = 0; d < 3; d++) {
-                const float hx = 0.5f * (float)((int64_t)G3.bmax[d] - (int64_t)G3.bmin[d]) * qf[d];
-                half2 = fmaf(hx, hx, half2);
-            }
-            ccx = 0.5f * ((float)G3.bmin[0] + (float)G3.bmax[0]) * qf[0];
-            ccy = 0.5f * ((float)G3.bmin[1] + (float)G3.bmax[1]) * qf[1];
-            ccz = 0.5f * ((float)G3.bmin[2] + (float)G3.bmax[2]) * qf[2];
-            const float Rm = (sqrtf(half2) + G3.hmax) * (1.0f + 1e-5f) + 8.0f * qm;
-            ball2 = Rm * Rm;
-        }
-
         long long rr[2];
-        {
-            const float cc[3] = {ccx, ccy, ccz};
-            item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, cc, ball2, qf, rr);
-        }
+        item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, cc0, ball2, qf, rr);
 
         Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
         Acc64 A64 = {0.0, 0.0, 0.0, 0};
@@ -566,12 +609,13 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
                     const int slot = cnt + __popc(m & lanemask_lt());
                     if (kMode >= 2) stage_pair_put((float *)stage, slot, L.sh, fx, fy, fz, __uint_as_float(Pj.w));
                     else stage[slot] = make_float4(fx, fy, fz, __uint_as_float(Pj.w));
-                    if (kF64) sidx[slot] = j;
+                    if (kF64 || kExp) sidx[slot] = j;
                 }
                 cnt += __popc(m);
                 if (cnt > kStage - 32) {
                     __syncwarp();
-                    flush<kMode, kKern>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+                    flush<kMode, kKern, kExp>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd,
+                                              hd * hd, S, a.pdbl, a);
                     staged += cnt;
                     cnt = 0;
                 }
@@ -579,7 +623,8 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         }
         __syncwarp();
         if (cnt > 0) {
-            flush<kMode, kKern>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd, S, a.pdbl);
+            flush<kMode, kKern, kExp>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd,
+                                      S, a.pdbl, a);
             staged += cnt;
         }
 
@@ -678,17 +723,40 @@ int density_blocks_per_sm(int precision, int direct_pct)
     }
 }
 
-template <int kMode>
+template <int kMode, bool kExp = false>
 void launch_mode(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
-    const int bytes = kWarps * warp_smem_bytes<kMode>();
-    if (a.kernel == 0) k_density<kMode, 0><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
-    else k_density<kMode, 1><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
+    const int bytes = kWarps * warp_smem_bytes<kMode, kExp>();
+    if (kExp) {
+        // the export instantiations are not prepared by density_blocks_per_sm; the persistent
+        // grid stays correct whatever number of its blocks are resident at once
+        cudaFuncSetAttribute(k_density<kMode, 0, kExp>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_density<kMode, 1, kExp>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
+    if (a.kernel == 0) k_density<kMode, 0, kExp><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
+    else k_density<kMode, 1, kExp><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
 }
 
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
-    switch (mode_of(a.precision, a.direct_pct)) {
+    const int mode = mode_of(a.precision, a.direct_pct);
+    if (a.nb_out) {
+        // neighbour export (test aid): the same pass with the recording instantiations; the
+        // per-lane queue of the non-default FP32 mode 1 has no export
+        if (mode == 1) return cudaErrorNotSupported;
+        if (mode == 0) {
+            launch_mode<0, true>(a, todo, st);
+        } else {
+            if (a.free_first) {
+                launch_mode<3, true>(a, todo, st);
+                if (a.launches) *a.launches += 1;
+            }
+            launch_mode<2, true>(a, todo, st);
+        }
+        if (a.launches) *a.launches += 1;
+        return cudaGetLastError();
+    }
+    switch (mode) {
     case 0: launch_mode<0>(a, todo, st); break;
     case 1: launch_mode<1>(a, todo, st); break;
     default:

@@ -78,6 +78,14 @@ struct SolveArgs {
     int cubic;                 // 1: equal fixed-point quanta in x, y, z (read by the kNN pass)
     int *launches;
     cudaEvent_t dens_ev[2];    // optional events recorded around the density launch
+    // neighbour-set export of sampled targets (test aid; nb_out == nullptr: off).  The density
+    // pass then also writes, for every target whose caller index i has nb_slot[i] = k >= 0, the
+    // caller indices of its in-h neighbours to nb_out[k * nb_max ..] and their number to
+    // nb_cnt[k] (counted in full; entries past nb_max are not written).
+    const int32_t *nb_slot;
+    int32_t *nb_out;
+    int32_t *nb_cnt;
+    int nb_max;
 };
 
 cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_iter, cudaStream_t st);
@@ -101,5 +109,9 @@ cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st)
 cudaError_t launch_knn_finish(const SolveArgs &a, cudaStream_t st);
 // starting radii of the kNN passes (entries <= 0 are estimated from the cell tables)
 cudaError_t launch_knn_init(const SolveArgs &a, const double *h_in, int max_iter, int k, cudaStream_t st);
+// neighbour export set-up: nb_slot (caller order, n entries) = -1 except nb_slot[sample[k]] = k;
+// counts zeroed; an index outside [0, n) or repeated sets kBadSample in the status word
+cudaError_t launch_nb_setup(const SolveArgs &a, int32_t *nb_slot, const int64_t *sample, int64_t n_sample,
+                            int32_t *nb_cnt, cudaStream_t st);
 
 }  // namespace sph

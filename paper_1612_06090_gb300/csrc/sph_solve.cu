@@ -311,6 +311,28 @@ __global__ void k_knn_finish(SolveArgs a)
     }
 }
 
+// Neighbour export set-up: every caller index maps to no sample row, then each sample claims
+// its target's entry (a claim that finds the entry taken, or an index outside [0, n), flags the
+// sample list as bad).
+__global__ void k_nb_clear(int32_t *__restrict__ nb_slot, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        nb_slot[i] = -1;
+}
+
+__global__ void k_nb_mark(int32_t *__restrict__ nb_slot, const int64_t *__restrict__ sample, int64_t n_sample,
+                          int64_t n, int32_t *__restrict__ nb_cnt, DevState *ds)
+{
+    int bad = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_sample;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = sample[k];
+        nb_cnt[k] = 0;
+        if (i < 0 || i >= n || atomicCAS(&nb_slot[i], -1, (int32_t)k) != -1) bad = 1;
+    }
+    if (bad) atomicOr(&ds->status, kBadSample);
+}
+
 int blocks_for(int64_t n, int cap)
 {
     int64_t b = (n + kThreads - 1) / kThreads;
@@ -390,6 +412,15 @@ cudaError_t launch_knn_init(const SolveArgs &a, const double *h_in, int max_iter
 {
     k_knn_init<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a, h_in, max_iter, k);
     if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nb_setup(const SolveArgs &a, int32_t *nb_slot, const int64_t *sample, int64_t n_sample,
+                            int32_t *nb_cnt, cudaStream_t st)
+{
+    k_nb_clear<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(nb_slot, a.n);
+    k_nb_mark<<<blocks_for(n_sample, a.grid_cap), kThreads, 0, st>>>(nb_slot, sample, n_sample, a.n, nb_cnt, a.ds);
+    if (a.launches) *a.launches += 2;
     return cudaGetLastError();
 }
 

@@ -260,11 +260,19 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     a.direct_pct = 0;
     a.launches = &launches;
     CUS(launch_solve_init(a, h_dev, 1, st));
+
+    // The sort flags bad positions and masses, the init flags a bad h.  Read the state word
+    // (into pageable host memory) and stop before the density pass if either is set: the
+    // pass's cell enumeration relies on every h lying in (0, min(box)/2).
+    DevState host{};
+    CUS(cudaMemcpyAsync(&host, c.ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CUS(cudaStreamSynchronize(st));
+    if (host.status | host.sort_status) return SPH_ERR_DEVICE_STATUS;
+
     CUS(launch_pass(a, 0, false, st));
     CUS(launch_scatter(a, nullptr, rho_out_dev, count_out_dev, nw_out_dev, dnw_out_dev, st));
 
-    // read the device status word into pageable host memory and wait for the results
-    DevState host{};
+    // wait for the results and read the state word again
     CUS(cudaMemcpyAsync(&host, c.ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     CUS(cudaStreamSynchronize(st));
     if (host.status | host.sort_status) return SPH_ERR_DEVICE_STATUS;

@@ -262,16 +262,50 @@ def plummer_groups(n_groups: int = 20000, seed: int = 4, nmin: int = 32, nmax: i
                           "a": a, "truncation_radius_over_a": trunc, "total": n})
 
 
-def clumpy_snapshots(n: int = 1 << 26, seed: int = 5, n_clumps: int = 4096,
-                     a_range=(1e-3, 1e-2), frac: float = 0.7, trunc: float = 50.0,
-                     drift: float = 1e-4, n_snapshots: int = 8, nngb: float = 64.0,
-                     tol: float = 2.0, snapshot: int = 0) -> Workload:
-    """Config c5: Plummer clumps (log-uniform scale radii) + background, with drift.
+def _parallel(fn, items):
+    """Run fn over items on a thread pool (NumPy's generators and ufuncs release the GIL)."""
+    import concurrent.futures
+    import os
 
-    Snapshot s adds s independent N(0, drift^2) steps per coordinate to snapshot 0 and
-    wraps; snapshots share the same particle identities, so an h solved on snapshot s-1
-    is a warm start for snapshot s.
-    """
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        list(ex.map(fn, items))
+
+
+_CHUNK = 1 << 22
+
+
+def _wrap_unit_inplace(pos: np.ndarray) -> None:
+    """Wrap every coordinate of a (3, n) array into [0, 1) in place (chunked, threaded).
+
+    x - floor(x) equals np.mod(x, 1.0) for the |x| < 2 that occur here; a tiny negative x
+    can round up to 1.0, which folds back to 0 as in _wrap."""
+    flat = pos.reshape(-1)
+
+    def one(k):
+        v = flat[k:k + _CHUNK]
+        v -= np.floor(v)
+        v[v >= 1.0] = 0.0
+
+    _parallel(one, range(0, flat.size, _CHUNK))
+
+
+def _add_drift_inplace(pos: np.ndarray, seed: int, step: int, drift: float) -> None:
+    """Add drift step `step` (>= 1): N(0, drift^2) per coordinate, drawn in chunks of 2^22
+    values from independent PCG64 streams seeded by (seed, step, chunk)."""
+    flat = pos.reshape(-1)
+
+    def one(k):
+        g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 17, step, k // _CHUNK])))
+        v = flat[k:k + _CHUNK]
+        d = g.standard_normal(size=v.shape[0])
+        d *= drift
+        v += d
+
+    _parallel(one, range(0, flat.size, _CHUNK))
+
+
+def _clumpy_base(n, seed, n_clumps, a_range, frac, trunc):
+    """Unwrapped snapshot-0 positions of config c5 (a fresh (3, n) array)."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     n_cl = int(round(frac * n))
     counts = _split_counts(n_cl, n_clumps)
@@ -285,55 +319,49 @@ def clumpy_snapshots(n: int = 1 << 26, seed: int = 5, n_clumps: int = 4096,
         o += k
     pos[:, n_cl:] = rng.uniform(0.0, 1.0, size=(3, n - n_cl))
     perm = rng.permutation(n)
-    pos = pos[:, perm]
-    drift_rng = np.random.default_rng(np.random.PCG64(seed * 1000 + 17))
-    for _ in range(snapshot):
-        pos += drift_rng.normal(0.0, drift, size=pos.shape)
-    pos = np.ascontiguousarray(_wrap(pos, (1.0, 1.0, 1.0)))
+    out = np.empty_like(pos)
+
+    def gather(d):
+        np.take(pos[d], perm, out=out[d])
+
+    _parallel(gather, range(3))
+    return out
+
+
+def clumpy_snapshot_series(n_snapshots: int = 8, n: int = 1 << 26, seed: int = 5, n_clumps: int = 4096,
+                           a_range=(1e-3, 1e-2), frac: float = 0.7, trunc: float = 50.0,
+                           drift: float = 1e-4, nngb: float = 64.0, tol: float = 2.0, first: int = 0):
+    """Yield snapshots first .. n_snapshots-1 of config c5 one after another.
+
+    Config c5: Plummer clumps (70 % of the particles, log-uniform scale radii, truncated at
+    `trunc` scale radii) + a uniform background in the periodic unit box.  Snapshot s adds s
+    independent N(0, drift^2) steps per coordinate to snapshot 0 and wraps; snapshots share
+    the same particle identities, so an h solved on snapshot s-1 is a warm start for
+    snapshot s.  Each yielded Workload owns its position array.
+    """
+    base = _clumpy_base(n, seed, n_clumps, a_range, frac, trunc)
+    mass = np.full(n, 1.0 / n)
     h0 = np.full(n, mean_density_h(nngb, float(n)))
-    return Workload("clumps4096", pos, np.full(n, 1.0 / n), h0, (1.0, 1.0, 1.0), True, nngb, tol,
-                    {"seed": seed, "n_clumps": n_clumps, "a_range": list(a_range),
-                     "drift": drift, "snapshot": snapshot, "n_snapshots": n_snapshots})
-
-
-def clumpy_snapshot_series(n_snapshots: int = 8, **kw):
-    """Yield snapshots 0 .. n_snapshots-1 of config c5 one after another.
-
-    Each yielded Workload equals clumpy_snapshots(snapshot=s, **kw) (same draws in the same
-    order) but the base particle set is generated once.
-    """
-    kw = {"seed": CONFIG_SEEDS["c5"], **kw}
-    kw.pop("snapshot", None)
-    base = clumpy_snapshots(snapshot=0, **kw)
-    # rebuild the unwrapped snapshot-0 positions exactly as clumpy_snapshots draws them
-    seed = kw.get("seed", CONFIG_SEEDS["c5"])
-    n = kw.get("n", 1 << 26)
-    n_clumps = kw.get("n_clumps", 4096)
-    a_range = kw.get("a_range", (1e-3, 1e-2))
-    frac = kw.get("frac", 0.7)
-    trunc = kw.get("trunc", 50.0)
-    drift = kw.get("drift", 1e-4)
-    rng = np.random.default_rng(np.random.PCG64(seed))
-    n_cl = int(round(frac * n))
-    counts = _split_counts(n_cl, n_clumps)
-    centres = rng.uniform(0.0, 1.0, size=(n_clumps, 3))
-    radii = np.exp(rng.uniform(math.log(a_range[0]), math.log(a_range[1]), size=n_clumps))
-    pos = np.empty((3, n))
-    o = 0
-    for c in range(n_clumps):
-        k = int(counts[c])
-        pos[:, o:o + k] = _plummer_offsets(rng, k, float(radii[c]), trunc) + centres[c][:, None]
-        o += k
-    pos[:, n_cl:] = rng.uniform(0.0, 1.0, size=(3, n - n_cl))
-    perm = rng.permutation(n)
-    pos = pos[:, perm]
-    drift_rng = np.random.default_rng(np.random.PCG64(seed * 1000 + 17))
+    meta = {"seed": seed, "n_clumps": n_clumps, "a_range": list(a_range), "drift": drift,
+            "n_snapshots": n_snapshots}
     for s in range(n_snapshots):
         if s > 0:
-            pos += drift_rng.normal(0.0, drift, size=pos.shape)
-        wl = Workload(base.name, np.ascontiguousarray(_wrap(pos, (1.0, 1.0, 1.0))), base.mass, base.h0,
-                      base.box, True, base.nngb, base.tol, {**base.meta, "snapshot": s})
-        yield wl
+            _add_drift_inplace(base, seed, s, drift)
+        if s < first:
+            continue
+        pos = base.copy()
+        _wrap_unit_inplace(pos)
+        yield Workload("clumps4096", pos, mass, h0, (1.0, 1.0, 1.0), True, nngb, tol, {**meta, "snapshot": s})
+
+
+def clumpy_snapshots(snapshot: int = 0, **kw) -> Workload:
+    """Config c5, snapshot `snapshot` alone (the same particles as clumpy_snapshot_series)."""
+    kw.setdefault("n_snapshots", max(8, snapshot + 1))
+    n_snap = kw.pop("n_snapshots")
+    for wl in clumpy_snapshot_series(n_snapshots=n_snap, first=snapshot, **kw):
+        wl.meta["n_snapshots"] = n_snap
+        return wl
+    raise ValueError(f"snapshot {snapshot} outside the series")
 
 
 def make(config: str, **kw):

@@ -71,3 +71,30 @@ def evaluate(pos, mass, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, chu
         dnw[s:s + chunk] = 4.0 * math.pi / 3.0 * sigma * dw.sum(axis=1) / hv
         count[s:s + chunk] = inside.sum(axis=1)
     return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
+
+
+def neighbours(pos, h, targets, box=(1.0, 1.0, 1.0), periodic=True, band=0.0):
+    """For each target i (at its own h_i), the particles j with r_ij < h_i (self included), and
+    the particles with |r_ij - h_i| <= band * h_i with their FP64 distances r_ij (minimum image).
+
+    Returns (inside, near): inside[k] is the sorted index array of target k's neighbours;
+    near[k] is a dict {j: r_ij} of the pairs within the band around h."""
+    pos = np.asarray(pos, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64)
+    tg = np.asarray(targets)
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), tg.shape)
+    inside, near = [], []
+    for k, i in enumerate(tg):
+        d = pos - pos[:, i:i + 1]
+        if periodic:
+            d = d - box[:, None] * np.round(d / box[:, None])
+        r2 = (d * d).sum(axis=0)
+        hk = h[k]
+        inside.append(np.flatnonzero(r2 < hk * hk))
+        if band > 0.0:
+            r = np.sqrt(r2)
+            m = np.flatnonzero(np.abs(r - hk) <= band * hk)
+            near.append({int(j): float(r[j]) for j in m})
+        else:
+            near.append({})
+    return inside, near

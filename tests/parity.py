@@ -53,14 +53,14 @@ def check_solve(pos, mass, box, periodic, nngb, tol, gpu, orc, targets, rtol, de
         assert np.all(d == 0), int(np.abs(d).max())
     else:
         e = oracle.evaluate(pos, mass, np.asarray(gpu["h"])[ok], box=box, periodic=periodic,
-                            targets=np.asarray(targets)[ok], near_rel=2e-6, mode=mode,
+                            targets=np.asarray(targets)[ok], near_rel=1e-6, mode=mode,
                             kernel=kernel or "m4")
         d = np.abs(np.asarray(gpu["count"], dtype=np.int64)[ok] - e["count"])
         assert np.all(d <= e["near"])
     if mism.any():
         idx = np.flatnonzero(mism)
         e = oracle.evaluate(pos, mass, np.asarray(gpu["h"])[idx], box=box, periodic=periodic,
-                            targets=np.asarray(targets)[idx], near_rel=2e-6, mode=mode,
+                            targets=np.asarray(targets)[idx], near_rel=1e-6, mode=mode,
                             kernel=kernel or "m4")
         assert np.all(np.abs(e["nw"] - nngb) <= tol + delta), np.abs(e["nw"] - nngb).max()
         assert np.max(rel_err(np.asarray(gpu["rho"])[idx], e["rho"])) <= rtol

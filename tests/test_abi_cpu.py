@@ -42,6 +42,26 @@ def test_exports_every_declared_function(B):
         assert hasattr(B.lib(), n)
 
 
+def test_probe_library_exports_its_header():
+    """libsph_probe.so (the FP32 rate probe the bench divides by) exports what sph_probe.h
+    declares."""
+    from paper_1612_06090_gb300 import build
+
+    build.build()
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sph_probe.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", text)))
+    assert names == ["sph_probe_fp32_fma"]
+    out = subprocess.run(["nm", "-D", "--defined-only", build.PROBE_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (sph_\w+)", out))
+    assert set(names) <= exported
+    lib = ctypes.CDLL(build.PROBE_PATH)
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    # argument checks answer before any device work
+    assert lib.sph_probe_fp32_fma(None, 0, 10, 0, ctypes.byref(tf), ctypes.byref(ms)) == 1
+    assert lib.sph_probe_fp32_fma(None, 8, 10, 0, None, ctypes.byref(ms)) == 1
+
+
 def test_struct_layout_matches_header(tmp_path, B):
     src = tmp_path / "layout.c"
     src.write_text(

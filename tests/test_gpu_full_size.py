@@ -50,7 +50,7 @@ def _sample_check(wl, g, n_samples, seed, precision, h0=None):
     fp64 = precision == B.SPH_PREC_FP64
     return check_solve(wl.pos, wl.mass, wl.box, True, wl.nngb, wl.tol, gs, o, tg,
                        rtol=1e-12 if fp64 else 1e-5, delta=(1e-9 if fp64 else 1e-5) * wl.nngb,
-                       max_mismatch_frac=0.05, count_exact=fp64, mode="brute"), o
+                       max_mismatch_frac=0.002, count_exact=fp64, mode="brute"), o
 
 
 @functools.lru_cache(maxsize=1)
@@ -82,7 +82,7 @@ def test_config5_clumps_67M_sampled_with_warm_start_snapshot():
                       mode="brute")
     gs = {k: g1[k][tg] for k in ("h", "rho", "count", "nw")}
     check_solve(wl1.pos, wl1.mass, wl1.box, True, wl1.nngb, wl1.tol, gs, o1, tg, rtol=1e-5,
-                delta=1e-5 * wl1.nngb, max_mismatch_frac=0.05, count_exact=False, mode="brute")
+                delta=1e-5 * wl1.nngb, max_mismatch_frac=0.002, count_exact=False, mode="brute")
 
 
 @pytest.mark.parametrize("precision", [B.SPH_PREC_FP32_KAHAN])
@@ -106,7 +106,7 @@ def test_config4_batched_groups_sampled(precision):
         assert np.all(o["status"] == 0)
         gs = {k: g[k][s0:e0] for k in ("h", "rho", "count", "nw")}
         check_solve(wl.pos[:, s0:e0], wl.mass[s0:e0], (0, 0, 0), False, 32.0, 1.0, gs, o,
-                    np.arange(e0 - s0), rtol=1e-5, delta=1e-5 * 32, max_mismatch_frac=0.05,
+                    np.arange(e0 - s0), rtol=1e-5, delta=1e-5 * 32, max_mismatch_frac=0.002,
                     count_exact=False)
 
 
@@ -127,5 +127,5 @@ def test_config3_lognormal_16M_knn_sampled():
     o = oracle.knn(wl.pos, wl.mass, 295, targets=tg, mode="brute")
     assert np.max(rel_err(g["h"][tg], o["h"])) <= 2e-6
     assert np.max(rel_err(g["rho"][tg], o["rho"])) <= 1e-5
-    e = oracle.evaluate(wl.pos, wl.mass, g["h"][tg], targets=tg, near_rel=2e-6, mode="brute")
+    e = oracle.evaluate(wl.pos, wl.mass, g["h"][tg], targets=tg, near_rel=1e-6, mode="brute")
     assert np.all(np.abs(g["count"][tg].astype(np.int64) - e["count"]) <= e["near"])

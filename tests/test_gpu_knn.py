@@ -5,7 +5,7 @@ density at that h.  FP64 forms every squared distance exactly as the oracle does
 K-th smallest value is unique, so h agrees bit for bit, counts exactly, and rho to summation
 order.  FP32 selects among FP32 squared distances of offsets quantised to box/2^32: h agrees
 to 2e-6 relative (another particle can be K-th only when its distance is that close), rho
-to 1e-5, and counts within the pairs the oracle finds within 2e-6 h of the boundary.
+to 1e-5, and counts within the pairs the oracle finds within 1e-6 h of the boundary.
 """
 import math
 
@@ -46,7 +46,7 @@ def gpu_knn(pos, mass, k, h0, precision, box=(1.0, 1.0, 1.0), kernel=B.SPH_KERNE
 def check_fp32(g, pos, mass, tg, k, o, kernel="m4"):
     assert np.max(rel_err(g["h"][tg], o["h"])) <= 2e-6
     assert np.max(rel_err(g["rho"][tg], o["rho"])) <= 1e-5
-    e = oracle.evaluate(pos, mass, g["h"][tg], targets=tg, near_rel=2e-6, kernel=kernel)
+    e = oracle.evaluate(pos, mass, g["h"][tg], targets=tg, near_rel=1e-6, kernel=kernel)
     assert np.all(np.abs(g["count"][tg].astype(np.int64) - e["count"]) <= e["near"])
 
 

@@ -5,7 +5,9 @@ neighbour decisions, same per-pair terms), so counts are exact and rho, N_w, h a
 summation-order rounding (<= 1e-12 relative).  FP32 mode forms offsets from 32-bit fixed
 point coordinates (quantum box/2^32) and sums FP32 terms with compensation; rho, N_w and h
 must agree to 1e-5 relative, and integer counts may differ only by pairs the oracle finds
-within 2e-6 h of the boundary.  Band-edge particles go through the check in parity.py.
+within 1e-6 h of the boundary (the bound derived for the FP32 distance test; the neighbour sets
+themselves are checked in test_gpu_neighbours.py).  Band-edge particles go through the check
+in parity.py; at most 0.2 % of the particles may take that route.
 """
 import math
 
@@ -76,7 +78,7 @@ def test_eval_fp32_against_oracle(scale):
     rng = np.random.default_rng(8)
     h = wl.h0 * scale * rng.uniform(0.9, 1.1, size=wl.n)
     g = gpu_eval(wl.pos, wl.mass, h, FP32)
-    o = oracle.evaluate(wl.pos, wl.mass, h, near_rel=2e-6)
+    o = oracle.evaluate(wl.pos, wl.mass, h, near_rel=1e-6)
     check_eval(g, o, rtol=1e-5, count_exact=False, near=o["near"])
     assert np.max(np.abs(g["dnw"] - o["dnw"]) / (np.abs(o["dnw"]) + 1.0 / h)) <= 1e-4
 
@@ -119,7 +121,7 @@ def test_anisotropic_periodic_box():
     o = oracle.evaluate(pos, mass, h, box=box)
     check_eval(g, o, rtol=1e-12, count_exact=True)
     g32 = gpu_eval(pos, mass, h, FP32, box=box)
-    o32 = oracle.evaluate(pos, mass, h, box=box, near_rel=2e-6)
+    o32 = oracle.evaluate(pos, mass, h, box=box, near_rel=1e-6)
     check_eval(g32, o32, rtol=1e-5, count_exact=False, near=o32["near"])
 
 
@@ -162,7 +164,7 @@ def test_solve_fp32_config1():
     assert g["status"] == B.SPH_OK
     o = oracle.solve(wl.pos, wl.mass, wl.h0)
     check_solve(wl.pos, wl.mass, wl.box, True, 64.0, 2.0, g, o, np.arange(wl.n), rtol=1e-5,
-                delta=1e-5 * 64, max_mismatch_frac=0.01, count_exact=False)
+                delta=1e-5 * 64, max_mismatch_frac=0.002, count_exact=False)
 
 
 @pytest.mark.parametrize("precision", [FP32, FP64])
@@ -179,7 +181,7 @@ def test_solve_config2_sampled(precision):
     rtol = 1e-12 if precision == FP64 else 1e-5
     check_solve(wl.pos, wl.mass, wl.box, True, 64.0, 2.0, gs, o, tg, rtol=rtol,
                 delta=(1e-9 if precision == FP64 else 1e-5) * 64,
-                max_mismatch_frac=0.02, count_exact=(precision == FP64))
+                max_mismatch_frac=0.002, count_exact=(precision == FP64))
 
 
 def test_fp32_and_fp64_gpu_agree_config2():
@@ -187,7 +189,7 @@ def test_fp32_and_fp64_gpu_agree_config2():
     a = gpu_solve(wl.pos, wl.mass, wl.h0, FP32)
     b = gpu_solve(wl.pos, wl.mass, wl.h0, FP64)
     same = (rel_err(a["h"], b["h"]) <= 1e-5)
-    assert same.mean() > 0.98
+    assert same.mean() > 0.998
     assert np.max(rel_err(a["rho"][same], b["rho"][same])) <= 1e-5
 
 
@@ -307,7 +309,7 @@ def test_batch_matches_oracle(precision):
     eh = rel_err(g["h"], o["h"])
     er = rel_err(g["rho"], o["rho"])
     mism = (eh > rtol) | (er > rtol)
-    assert mism.mean() <= 0.02
+    assert mism.mean() <= 0.002
     if precision == FP64:
         np.testing.assert_array_equal(g["count"][~mism], o["count"][~mism])
     # every group's answers lie in its band
@@ -428,7 +430,7 @@ def test_wendland_c6_eval_against_oracle(precision):
         o = oracle.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6")
         check_eval(g, o, rtol=1e-12, count_exact=True)
     else:
-        o = oracle.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6", near_rel=2e-6)
+        o = oracle.evaluate(wl.pos, wl.mass, h, kernel="wendland_c6", near_rel=1e-6)
         check_eval(g, o, rtol=1e-5, count_exact=False, near=o["near"])
 
 
@@ -448,7 +450,7 @@ def test_wendland_c6_solve_clusters_sampled(precision):
     gs = {k: g[k][tg] for k in ("h", "rho", "count", "nw")}
     fp64 = precision == FP64
     check_solve(wl.pos, wl.mass, wl.box, True, 295.0, 5.0, gs, o, tg, rtol=1e-12 if fp64 else 1e-5,
-                delta=(1e-9 if fp64 else 1e-5) * 295.0, max_mismatch_frac=0.03, count_exact=fp64,
+                delta=(1e-9 if fp64 else 1e-5) * 295.0, max_mismatch_frac=0.002, count_exact=fp64,
                 kernel="wendland_c6")
 
 
