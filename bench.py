@@ -976,7 +976,7 @@ def run_replay(args):
     def snap_of(g):
         return 1 + g % (n_snap - 1)
 
-    def timed(slv, steps, warmup, g0=0):
+    def timed(slv, steps, warmup, g0=0, nvtx_name="replay_timed"):
         """warmup + steps replay steps from global step index g0; CUDA events around each
         step's sort + solve, on the library's stream."""
         saved = {}
@@ -991,6 +991,8 @@ def run_replay(args):
         stats = []
         barrier(world)
         torch.cuda.synchronize()
+        # an NVTX range names the timed steps for profilers (ncu --nvtx --nvtx-include)
+        torch.cuda.nvtx.range_push(nvtx_name)
         w0 = time.perf_counter()
         for k in range(steps):
             g = g0 + warmup + k
@@ -1003,6 +1005,7 @@ def run_replay(args):
         torch.cuda.synchronize()
         barrier(world)
         wall = time.perf_counter() - w0
+        torch.cuda.nvtx.range_pop()
         if "h1" not in saved:
             # no warm-up step replayed snapshot 1: replay it once more, untimed, for the
             # FP32 / FP64 comparison
@@ -1023,7 +1026,7 @@ def run_replay(args):
     # ---- the same replay with the host-driven pass loop: per-pass density-kernel events ----
     sh = solver(B.SPH_PREC_FP32_KAHAN, False)
     sh._check(B.sph_set_tuning(sh.ctx, B.SphTuning(**tuning)))
-    msh, sth, _, _ = timed(sh, n_snap - 1, 1, g0=0)
+    msh, sth, _, _ = timed(sh, n_snap - 1, 1, g0=0, nvtx_name="replay_host_loop")
     sh.close()
     dens_ms = statistics.mean(x["density_ms"] for x in sth)
     pairs = statistics.mean(x["pair_evals"] for x in sth)

@@ -94,8 +94,9 @@ typedef struct {
 
 typedef struct sph_ctx sph_ctx;
 
-/* Knobs of the spatial decomposition, set by the autotuner or by hand.  They change speed,
- * never results beyond summation order.  Defaults: {0, 3, 1, 0}. */
+/* Knobs of the spatial decomposition and of the density kernels' launch, set by the
+ * autotuner or by hand.  They change speed, never results beyond summation order.
+ * Defaults: {0, 3, 1, 0, 0, 32, 256, 0}. */
 typedef struct {
     int32_t group_shift;  /* a work item gathers todo targets that share an octree cell of edge
                              >= h / 2^group_shift (-2..3)                                     */
@@ -107,6 +108,15 @@ typedef struct {
                              (fastest measured); otherwise in-h pairs are queued per lane
                              until more than this percentage of an item's first tests fall
                              within h (1..101; 101 = always queue).  FP64 always queues.      */
+    int32_t item_cap;     /* 0: a work item is a run of todo targets sharing the octree cell of
+                             their grouping level; 2..64: the item is the coarsest octree cell,
+                             no coarser than that level, holding at most item_cap todo targets
+                             (compact items: fewer candidate tests per neighbour found)          */
+    int32_t item_max;     /* targets per work item at most: 1, 2, 4, 8, 16 or 32 (a target then
+                             gets at least 32 / item_max lanes of the warp)                      */
+    int32_t block_threads;/* threads per block of the density kernels: 64, 128 or 256           */
+    int32_t blocks_per_sm;/* resident blocks per SM of the persistent density grid, 0 = as many
+                             as fit (occupancy); larger values are clamped to that              */
 } sph_tuning;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
@@ -129,12 +139,16 @@ sph_status sph_get_tuning(const sph_ctx *ctx, sph_tuning *out);
 sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
 
 /* Autotuner: the GPU counterpart of the work distribution choices of Sec. IV-A (dynamic
- * scheduling of uneven per-particle work).  Time the grouping level (group_shift -1..1) and the candidate cell size
- * (cell_div 2..3) with full solves from h_dev (n doubles, caller order, read only) on the
- * particles of the last sph_sort, keep the fastest in the context and, when the context has
- * a tune_cache file, append it there; sph_sort applies the last cached entry that matches
- * the GPU, the particle-count bucket (floor log2 n), periodic and precision.  best may be
- * NULL.  Results never change beyond summation order.  Errors: as sph_density_solve. */
+ * scheduling of uneven per-particle work).  Times full solves from h_dev (n doubles, caller
+ * order, read only) on the particles of the last sph_sort while it varies, one knob at a
+ * time from the current tuning and keeping the best value of each (two rounds): the item
+ * cap (0, 16, 32, 64), targets per item (8, 16, 32), the grouping level (group_shift
+ * -1..1), the candidate cell size (cell_div 2..3), threads per block (128, 256) and
+ * resident blocks per SM (all that fit, or one fewer).  Keeps the fastest tuning in the
+ * context and, when the context has a tune_cache file, appends it there; sph_sort applies
+ * the last cached entry that matches the GPU, the particle-count bucket (floor log2 n),
+ * periodic and precision.  best may be NULL.  Results never change beyond summation order.
+ * Errors: as sph_density_solve. */
 sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best);
 
 /* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix

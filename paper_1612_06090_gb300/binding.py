@@ -98,6 +98,10 @@ class SphTuning(ctypes.Structure):
         ("cell_div", ctypes.c_int32),
         ("table_extra", ctypes.c_int32),
         ("direct_pct", ctypes.c_int32),
+        ("item_cap", ctypes.c_int32),
+        ("item_max", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

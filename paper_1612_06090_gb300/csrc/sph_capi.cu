@@ -70,11 +70,13 @@ struct sph_ctx {
         sph_tuning tuning{};
         KeyLayout kl{};
     } graph_key;
-    sph_tuning tuning{0, 3, 1, 0};
+    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
     int grid_cap = 0;
-    int density_grid[3] = {0, 0, 0};  // FP64, FP32 with queue, FP32 direct
+    // resident density blocks per SM: [FP64, FP32 with queue, FP32 direct][64, 128, 256 threads]
+    // (0 = not asked yet)
+    int occupancy[3][3] = {};
 };
 
 namespace {
@@ -233,10 +235,18 @@ SolveArgs solve_args(sph_ctx *c)
     a.grid_cap = c->grid_cap;
     a.precision = c->params.precision;
     a.kernel = c->params.kernel;
-    a.density_grid = c->density_grid[c->params.precision == SPH_PREC_FP64 ? 0
-                                      : c->tuning.direct_pct == 0           ? 2
-                                                                            : 1];
-    a.gmax = 32;
+    {
+        const int mode = c->params.precision == SPH_PREC_FP64 ? 0 : c->tuning.direct_pct == 0 ? 2 : 1;
+        const int bt = c->tuning.block_threads;
+        const int ti = bt == 64 ? 0 : bt == 128 ? 1 : 2;
+        int &occ = c->occupancy[mode][ti];
+        if (occ == 0) occ = density_blocks_per_sm(c->params.precision, c->tuning.direct_pct, bt);
+        const int bps = c->tuning.blocks_per_sm > 0 && c->tuning.blocks_per_sm < occ ? c->tuning.blocks_per_sm : occ;
+        a.density_grid = c->num_sms * bps;
+        a.block_threads = bt;
+    }
+    a.gmax = c->tuning.item_max;
+    a.item_cap = c->tuning.item_cap;
     a.group_shift = c->tuning.group_shift;
     a.cell_div = c->tuning.cell_div;
     a.direct_pct = c->tuning.direct_pct;
@@ -255,8 +265,9 @@ int table_level(int64_t n, int lmax, int extra)
     return lc;
 }
 
-// Autotuner cache: one line per result, "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp";
-// the last matching line wins.
+// Autotuner cache: one line per result,
+// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs" (the sph_tuning fields in
+// order); the last matching line wins.
 std::string cache_key(const sph_ctx *c, int64_t n)
 {
     int b = 0;
@@ -275,8 +286,9 @@ bool cache_lookup(const sph_ctx *c, int64_t n, sph_tuning *t)
     char line[512], k[300];
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
-        sph_tuning x{};
-        if (sscanf(line, "%299s %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra, &x.direct_pct) == 5 &&
+        sph_tuning x = c->tuning;
+        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra,
+                   &x.direct_pct, &x.item_cap, &x.item_max, &x.block_threads, &x.blocks_per_sm) == 9 &&
             key == k) {
             *t = x;
             found = true;
@@ -291,14 +303,19 @@ void cache_store(const sph_ctx *c, int64_t n, const sph_tuning &t)
     if (c->tune_cache.empty()) return;
     FILE *f = fopen(c->tune_cache.c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div, t.table_extra, t.direct_pct);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div, t.table_extra,
+            t.direct_pct, t.item_cap, t.item_max, t.block_threads, t.blocks_per_sm);
     fclose(f);
 }
 
 bool tuning_ok(const sph_tuning *t)
 {
+    const bool pow2 = t && t->item_max >= 1 && t->item_max <= 32 && (t->item_max & (t->item_max - 1)) == 0;
     return t && t->group_shift >= -2 && t->group_shift <= 3 && t->cell_div >= 1 && t->cell_div <= 3 &&
-           t->table_extra >= 0 && t->table_extra <= 1 && t->direct_pct >= 0 && t->direct_pct <= 101;
+           t->table_extra >= 0 && t->table_extra <= 1 && t->direct_pct >= 0 && t->direct_pct <= 101 &&
+           (t->item_cap == 0 || (t->item_cap >= 2 && t->item_cap <= 64)) && pow2 &&
+           (t->block_threads == 64 || t->block_threads == 128 || t->block_threads == 256) &&
+           t->blocks_per_sm >= 0 && t->blocks_per_sm <= 32;
 }
 
 sph_status read_state(sph_ctx *c)
@@ -542,9 +559,6 @@ sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_str
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(SPH_ERR_CUDA);
     c->grid_cap = c->num_sms * 16;
-    c->density_grid[0] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP64, 0);
-    c->density_grid[1] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN, 1);
-    c->density_grid[2] = c->num_sms * density_blocks_per_sm(SPH_PREC_FP32_KAHAN, 0);
     if (cudaMemset(c->ds, 0, sizeof(DevState)) != cudaSuccess) return bail(SPH_ERR_CUDA);
     *out = c;
     return SPH_OK;
@@ -701,43 +715,87 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
     CU(ctx, cudaMemcpyAsync(ctx->segs, ctx->seg_pinned, sizeof(SegInfo), cudaMemcpyHostToDevice, st),
        "uploading the segment");
     const sph_tuning base = ctx->tuning;
+    // one full solve from h_dev with tuning t: its device time in ms (< 0 on failure, with the
+    // status in *err)
+    auto time_one = [&](const sph_tuning &t, sph_status *err) -> float {
+        ctx->tuning = t;
+        SolveArgs a = solve_args(ctx);
+        *err = SPH_OK;
+        cudaError_t e = cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2], st);
+        if (e == cudaSuccess) e = launch_solve_init(a, h_dev, ctx->params.max_iter, st);
+        if (e != cudaSuccess) {
+            *err = cuda_fail(ctx, e, "autotune solve");
+            return -1.f;
+        }
+        int passes = 0;
+        sph_status s = host_passes(ctx, a, false, &passes);
+        if (s == SPH_OK) {
+            e = cudaEventRecord(ctx->ev[3], st);
+            if (e != cudaSuccess) s = cuda_fail(ctx, e, "event");
+        }
+        if (s == SPH_OK) s = read_state(ctx);
+        if (s == SPH_OK && (ctx->ds_host->status | ctx->ds_host->sort_status))
+            s = device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
+        float ms = -1.f;
+        if (s == SPH_OK) {
+            e = cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+            if (e != cudaSuccess) s = cuda_fail(ctx, e, "event time");
+        }
+        *err = s;
+        return s == SPH_OK ? ms : -1.f;
+    };
+    // one knob at a time from the current tuning, two rounds; a change is kept only when it
+    // saves more than 1 % (timing noise)
     sph_tuning best = base;
-    float best_ms = -1.f;
-    // knobs that need no re-sort: grouping level and candidate cell size (FP32 always
-    // evaluates directly; FP64 always queues)
-    for (int gs = -1; gs <= 1; gs++) {
-        for (int cd = 2; cd <= 3; cd++) {
-            sph_tuning t = base;
-            t.group_shift = gs;
-            t.cell_div = cd;
-            t.direct_pct = 0;
-            ctx->tuning = t;
-            SolveArgs a = solve_args(ctx);
-            CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
-            CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
-            CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
-            CU(ctx, launch_solve_init(a, h_dev, ctx->params.max_iter, st), "init");
-            int passes = 0;
-            sph_status s = host_passes(ctx, a, false, &passes);
-            if (s != SPH_OK) {
-                ctx->tuning = base;
-                return s;
+    best.direct_pct = 0;  // FP32 evaluates directly (FP64 always queues)
+    sph_status err = SPH_OK;
+    float best_ms = time_one(best, &err);
+    if (best_ms < 0.f) {
+        ctx->tuning = base;
+        return err;
+    }
+    const int mode = ctx->params.precision == SPH_PREC_FP64 ? 0 : 2;
+    for (int round = 0; round < 2; round++) {
+        for (int knob = 0; knob < 6; knob++) {
+            int vals[4];
+            int nv = 0;
+            switch (knob) {
+            case 0: vals[0] = 0, vals[1] = 16, vals[2] = 32, vals[3] = 64, nv = 4; break;  // item_cap
+            case 1: vals[0] = 8, vals[1] = 16, vals[2] = 32, nv = 3; break;                // item_max
+            case 2: vals[0] = -1, vals[1] = 0, vals[2] = 1, nv = 3; break;                 // group_shift
+            case 3: vals[0] = 2, vals[1] = 3, nv = 2; break;                               // cell_div
+            case 4: vals[0] = 128, vals[1] = 256, nv = 2; break;                           // block_threads
+            default: {                                                                     // blocks_per_sm
+                const int bt = best.block_threads;
+                const int ti = bt == 64 ? 0 : bt == 128 ? 1 : 2;
+                int &occ = ctx->occupancy[mode][ti];
+                if (occ == 0) occ = density_blocks_per_sm(ctx->params.precision, 0, bt);
+                vals[0] = 0;
+                nv = 1;
+                if (occ > 1) vals[nv++] = occ - 1;
             }
-            CU(ctx, cudaEventRecord(ctx->ev[3], st), "event");
-            s = read_state(ctx);
-            if (s != SPH_OK) {
-                ctx->tuning = base;
-                return s;
             }
-            if (ctx->ds_host->status | ctx->ds_host->sort_status) {
-                ctx->tuning = base;
-                return device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
-            }
-            float ms = 0.f;
-            CU(ctx, cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]), "event time");
-            if (best_ms < 0.f || ms < best_ms) {
-                best_ms = ms;
-                best = t;
+            for (int v = 0; v < nv; v++) {
+                sph_tuning t = best;
+                int *field = knob == 0   ? &t.item_cap
+                             : knob == 1 ? &t.item_max
+                             : knob == 2 ? &t.group_shift
+                             : knob == 3 ? &t.cell_div
+                             : knob == 4 ? &t.block_threads
+                                         : &t.blocks_per_sm;
+                if (*field == vals[v]) continue;
+                *field = vals[v];
+                const float ms = time_one(t, &err);
+                if (ms < 0.f) {
+                    ctx->tuning = base;
+                    return err;
+                }
+                if (ms < 0.99f * best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
             }
         }
     }

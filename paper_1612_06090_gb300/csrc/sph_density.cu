@@ -696,45 +696,52 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
 
 }  // namespace
 
+// Every warp works on its own items, so a block is only a bundle of warps: the block size is a
+// launch choice (64, 128 or 256 threads, up to the launch bound), with each warp's shared
+// memory carved from the block's.
 template <int kMode, int kKern>
-int blocks_per_sm()
+int blocks_per_sm(int threads)
 {
-    const int bytes = kWarps * warp_smem_bytes<kMode>();
-    cudaFuncSetAttribute(k_density<kMode, kKern>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int bytes = (threads / 32) * warp_smem_bytes<kMode>();
+    // the attribute is set for the largest block, which covers every smaller one
+    cudaFuncSetAttribute(k_density<kMode, kKern>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kWarps * warp_smem_bytes<kMode>());
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<kMode, kKern>, kThreads, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<kMode, kKern>, threads, bytes);
     return b > 0 ? b : 1;
 }
 
 int mode_of(int precision, int direct_pct) { return precision == 0 ? 0 : direct_pct == 0 ? 2 : 1; }
 
-int density_blocks_per_sm(int precision, int direct_pct)
+int density_blocks_per_sm(int precision, int direct_pct, int threads)
 {
+    if (threads != 64 && threads != 128) threads = kThreads;
     // both kernels' attributes are set; the grid follows the M4 instantiation (the persistent
     // grid is correct for any size, the work queue balances it)
     switch (mode_of(precision, direct_pct)) {
-    case 0: blocks_per_sm<0, 1>(); return blocks_per_sm<0, 0>();
-    case 1: blocks_per_sm<1, 1>(); return blocks_per_sm<1, 0>();
+    case 0: blocks_per_sm<0, 1>(threads); return blocks_per_sm<0, 0>(threads);
+    case 1: blocks_per_sm<1, 1>(threads); return blocks_per_sm<1, 0>(threads);
     default:
-        blocks_per_sm<3, 1>();
-        blocks_per_sm<3, 0>();
-        blocks_per_sm<2, 1>();
-        return blocks_per_sm<2, 0>();
+        blocks_per_sm<3, 1>(threads);
+        blocks_per_sm<3, 0>(threads);
+        blocks_per_sm<2, 1>(threads);
+        return blocks_per_sm<2, 0>(threads);
     }
 }
 
 template <int kMode, bool kExp = false>
 void launch_mode(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
-    const int bytes = kWarps * warp_smem_bytes<kMode, kExp>();
+    const int threads = (a.block_threads == 64 || a.block_threads == 128) ? a.block_threads : kThreads;
+    const int bytes = (threads / 32) * warp_smem_bytes<kMode, kExp>();
     if (kExp) {
         // the export instantiations are not prepared by density_blocks_per_sm; the persistent
         // grid stays correct whatever number of its blocks are resident at once
         cudaFuncSetAttribute(k_density<kMode, 0, kExp>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         cudaFuncSetAttribute(k_density<kMode, 1, kExp>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     }
-    if (a.kernel == 0) k_density<kMode, 0, kExp><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
-    else k_density<kMode, 1, kExp><<<a.density_grid, kThreads, bytes, st>>>(a, todo);
+    if (a.kernel == 0) k_density<kMode, 0, kExp><<<a.density_grid, threads, bytes, st>>>(a, todo);
+    else k_density<kMode, 1, kExp><<<a.density_grid, threads, bytes, st>>>(a, todo);
 }
 
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st)

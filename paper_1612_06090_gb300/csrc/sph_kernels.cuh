@@ -67,6 +67,9 @@ struct SolveArgs {
     int grid_cap;
     int density_grid;          // persistent blocks of the density kernels
     int gmax;                  // targets per work item (<= 32)
+    int item_cap;              // 0: items follow the grouping level; else the coarsest octree
+                               // cell (not coarser than that level) with <= item_cap todo targets
+    int block_threads;         // threads per block of the density kernels (64, 128 or 256)
     int group_shift;           // items group targets sharing an octree cell of edge >= h / 2^shift
     int cell_div;              // candidate cells have an edge >= (query extent) / cell_div
     int direct_pct;            // in-h percentage of the first tests above which the pair loop
@@ -98,7 +101,8 @@ cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, i
 
 // sph_density.cu
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st);
-int density_blocks_per_sm(int precision, int direct_pct);
+// resident blocks per SM of the density kernel of this precision / mode at this block size
+int density_blocks_per_sm(int precision, int direct_pct, int block_threads = 256);
 // k-nearest-neighbour pass over todo (one warp per target): selects h for targets whose
 // search radius holds K..knn_capacity candidates, adapts the radius of the others
 cudaError_t launch_knn(const SolveArgs &a, const int32_t *todo, int k, cudaStream_t st);

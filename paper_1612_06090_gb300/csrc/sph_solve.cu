@@ -227,6 +227,119 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
     }
 }
 
+// Number of leading octree levels two keys share: -1 when they lie in different segments,
+// kl.lmax when they are equal.  Two keys share the level-L cell iff the result is >= L.
+__device__ __forceinline__ int common_levels(uint64_t a, uint64_t b, const KeyLayout &kl)
+{
+    const uint64_t x = a ^ b;
+    if (x == 0ull) return kl.lmax;
+    const int lz = __clzll((long long)x) - (64 - kl.key_bits);
+    if (lz < kl.seg_bits) return -1;
+    return (lz - kl.seg_bits) / 3;
+}
+
+constexpr int kCapTile = 256;  // todo entries per tile of the capped item rule (one per thread)
+constexpr int kCapMax = 64;    // largest item cap
+constexpr int kCapLevels = 6;  // levels examined below a target's grouping level
+
+// Work-item heads with the item cap: an item is the coarsest octree cell, no coarser than the
+// targets' grouping level and at most kCapLevels - 1 levels finer, whose run of consecutive
+// todo targets has at most item_cap entries.  Runs nest (a cell's run is a union of its
+// children's runs), so every target of such a run finds the same cell, and items are compact
+// groups of nearby targets whatever the local density.  A run that is still too long at the
+// finest level examined is cut every gmax targets from its start.  Each tile of the todo list
+// is staged with its keys in shared memory; a target finds its run at every examined level
+// with one walk of at most item_cap entries in each direction.
+__global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, const int32_t *__restrict__ todo)
+{
+    constexpr int kHalo = kCapMax + 2;
+    __shared__ uint64_t sk[kCapTile + 2 * kHalo];
+    __shared__ int sl[kCapTile + 1];  // entries base - 1 .. base + kCapTile - 1: level | big << 8
+    const int T = a.ds->pass_count;
+    const int cap = a.item_cap < kCapMax ? a.item_cap : kCapMax;
+    const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
+    const int ntiles = (T + kCapTile - 1) / kCapTile;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int base = tile * kCapTile;
+        // sk[i] holds the key of entry base - kHalo + i (positions outside [0, T) are never read
+        // as keys: the walks stop at 0 and at T)
+        for (int i = threadIdx.x; i < kCapTile + 2 * kHalo; i += blockDim.x) {
+            const int t = base - kHalo + i;
+            sk[i] = (t >= 0 && t < T) ? a.key[todo[t]] : 0ull;
+        }
+        __syncthreads();
+        // levels shared by entry u and its predecessor (-1: u starts a run at every level)
+        auto dprev = [&](int u) -> int {
+            if (u <= 0 || u >= T) return -1;
+            const int i = u - base + kHalo;
+            return common_levels(sk[i - 1], sk[i], a.kl);
+        };
+        // level of entry t, and the distance from the start of its item's run (-1: unknown)
+        auto level_of = [&](int t, int &from_start) -> int {
+            from_start = -1;
+            const int p = todo[t];
+            const uint64_t k = a.key[p];
+            int lh;
+            uint64_t pre;
+            bool big;
+            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, lh, pre, big, ctab0);
+            if (big) return lh | (1 << 8);
+            const int nl = a.kl.lmax - lh + 1 < kCapLevels ? a.kl.lmax - lh + 1 : kCapLevels;
+            // back[k]: entries from the start of the level-(lh + k) run to t inclusive;
+            // fwd[k]: entries after t in that run; cap + 1 stands for "more than cap"
+            int back[kCapLevels], fwd[kCapLevels];
+#pragma unroll
+            for (int q = 0; q < kCapLevels; q++) back[q] = fwd[q] = cap + 1;
+            // walking outwards, finer levels meet their boundary first: levels kres.. are resolved
+            int kres = nl;
+            for (int j = 0; j <= cap && kres > 0; j++) {
+                if (t - j < 0) break;
+                const int d = dprev(t - j);
+#pragma unroll
+                for (int q = kCapLevels - 1; q >= 0; q--)
+                    if (q < kres && d < lh + q) {
+                        back[q] = j + 1;
+                        kres = q;
+                    }
+            }
+            kres = nl;
+            for (int j = 1; j <= cap && kres > 0; j++) {
+                const int d = dprev(t + j);  // -1 past the end of the list
+#pragma unroll
+                for (int q = kCapLevels - 1; q >= 0; q--)
+                    if (q < kres && d < lh + q) {
+                        fwd[q] = j - 1;
+                        kres = q;
+                    }
+            }
+            int q = 0;
+            while (q < nl - 1 && back[q] + fwd[q] > cap) q++;
+            if (back[q] <= cap) from_start = back[q] - 1;
+            return lh + q;
+        };
+        const int t = base + threadIdx.x;
+        int from_start = -1;
+        if (t < T) sl[threadIdx.x + 1] = level_of(t, from_start);
+        if (threadIdx.x == 0 && t > 0 && t - 1 < T) {
+            int dummy;
+            sl[0] = level_of(t - 1, dummy);
+        }
+        __syncthreads();
+        if (t < T) {
+            const int me = sl[threadIdx.x + 1];
+            int head = t == 0 || (me >> 8) != 0;
+            if (!head) {
+                const int prev = sl[threadIdx.x];
+                const int lvl = me & 0xff;
+                head = (prev >> 8) != 0 || (prev & 0xff) != lvl || dprev(t) < lvl;
+                if (!head) head = from_start >= 0 ? from_start % a.gmax == 0 : t % a.gmax == 0;
+            }
+            a.flags[t] = head;
+        }
+        __syncthreads();
+    }
+}
+
 // mark_for_recomputation: band test, bracket, Newton or fallback, box limit (FP64, IEEE
 // roundings spelled out so no product is fused into an FMA).
 __global__ void k_h_update(SolveArgs a, const int32_t *__restrict__ todo)
@@ -354,7 +467,8 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
     const int32_t *todo = a.todo[cur];
     const int grid = blocks_for(a.n, a.grid_cap);
     k_pass_begin<<<1, 1, 0, st>>>(a.ds, a.free_first);
-    k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
+    if (a.item_cap > 0) k_item_flags_capped<<<grid, kCapTile, 0, st>>>(a, todo);
+    else k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
     if (a.launches) *a.launches += 2;
     // item starts = positions of the head flags
     cudaError_t e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->pass_count,

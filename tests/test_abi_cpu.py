@@ -70,15 +70,19 @@ def test_struct_layout_matches_header(tmp_path, B):
         ' printf("%zu %zu %zu %zu %zu\\n", sizeof(sph_params), offsetof(sph_params, nngb),'
         " offsetof(sph_params, max_iter), offsetof(sph_params, tune_cache), sizeof(sph_stats));\n"
         ' printf("%zu %zu %zu\\n", offsetof(sph_stats, todo_per_pass), offsetof(sph_stats, pair_evals),'
-        " offsetof(sph_stats, solve_ms));\n return 0; }\n")
+        " offsetof(sph_stats, solve_ms));\n"
+        ' printf("%zu %zu %zu\\n", sizeof(sph_tuning), offsetof(sph_tuning, item_cap),'
+        " offsetof(sph_tuning, blocks_per_sm));\n return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
     P, S = B.SphParams, B.SphStats
     assert [int(v) for v in a.split()] == [ctypes.sizeof(P), P.nngb.offset, P.max_iter.offset,
                                            P.tune_cache.offset, ctypes.sizeof(S)]
     assert [int(v) for v in b.split()] == [S.todo_per_pass.offset, S.pair_evals.offset, S.solve_ms.offset]
+    U = B.SphTuning
+    assert [int(v) for v in c.split()] == [ctypes.sizeof(U), U.item_cap.offset, U.blocks_per_sm.offset]
 
 
 def test_status_strings(B):
