@@ -462,6 +462,10 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         const int t0 = a.items[it];
         const int t1 = it + 1 < n_items ? a.items[it + 1] : todo_count;
         const int G = t1 - t0;
+        if (G < 1 || G > 32) {  // the item rules never make one; report, never overrun
+            if (lane == 0) atomicOr(&a.ds->status, 8);
+            continue;
+        }
         int Gp = 1;
         while (Gp < G) Gp <<= 1;
         LaneTarget L;

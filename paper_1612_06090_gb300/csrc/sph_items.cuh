@@ -126,16 +126,17 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
     }
 }
 
-// Ranges of the item's cells; lane holds cells `lane` and `lane + 32`.  A cell that lies
+// Ranges of the item's cells; lane holds cells lane + 32 k, k < K.  A cell that lies
 // entirely outside the staging ball (centre cc, squared radius ball2, both in the FP32 offset
 // units of the item) can hold no candidate, so its range is left empty: no lookup, no loads.
 // The test only drops cells whose nearest point is farther than the ball radius by a
 // relative 1e-4, far above the rounding of the FP32 cell bounds (a few 1e-7 of the extent).
+template <int K = 2>
 __device__ __forceinline__ void item_ranges(const ItemGeom &G, int g, const SegInfo &S,
                                             const KeyLayout &kl, const int32_t *__restrict__ ctab,
                                             const uint64_t *__restrict__ key, int ncell,
                                             const float cc[3], float ball2, const float qf[3],
-                                            long long r[2])
+                                            long long r[K])
 {
     const int lane = lane_id();
     const uint32_t cmask = (uint32_t)((1ull << G.level) - 1);
@@ -147,7 +148,7 @@ __device__ __forceinline__ void item_ranges(const ItemGeom &G, int g, const SegI
         c0f[d] = (float)G.cstart[d] * qf[d];
     }
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < K; k++) {
         const int c = lane + 32 * k;
         r[k] = 0;
         if (c < ncell) {

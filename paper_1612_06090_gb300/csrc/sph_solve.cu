@@ -246,8 +246,10 @@ constexpr int kCapLevels = 6;  // levels examined below a target's grouping leve
 // targets' grouping level and at most kCapLevels - 1 levels finer, whose run of consecutive
 // todo targets has at most item_cap entries.  Runs nest (a cell's run is a union of its
 // children's runs), so every target of such a run finds the same cell, and items are compact
-// groups of nearby targets whatever the local density.  A run that is still too long at the
-// finest level examined is cut every gmax targets from its start.  Each tile of the todo list
+// groups of nearby targets whatever the local density.  A run that fits is cut every gmax
+// targets from its start (when item_cap > gmax); a run still longer than item_cap at the finest
+// level examined is cut at every multiple of gmax in the todo list.  Both are properties of the
+// run, so all its members apply the same cut and no item exceeds gmax.  Each tile of the todo list
 // is staged with its keys in shared memory; a target finds its run at every examined level
 // with one walk of at most item_cap entries in each direction.
 __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, const int32_t *__restrict__ todo)
@@ -274,7 +276,8 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
             const int i = u - base + kHalo;
             return common_levels(sk[i - 1], sk[i], a.kl);
         };
-        // level of entry t, and the distance from the start of its item's run (-1: unknown)
+        // level of entry t, and the distance from the start of its item's run (-1: the run is
+        // longer than item_cap)
         auto level_of = [&](int t, int &from_start) -> int {
             from_start = -1;
             const int p = todo[t];
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
             }
             int q = 0;
             while (q < nl - 1 && back[q] + fwd[q] > cap) q++;
-            if (back[q] <= cap) from_start = back[q] - 1;
+            if (back[q] + fwd[q] <= cap) from_start = back[q] - 1;
             return lh + q;
         };
         const int t = base + threadIdx.x;
