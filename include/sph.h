@@ -69,7 +69,15 @@ typedef struct {
     int32_t max_iter;    /* passes, 1..64                                                  */
     int32_t precision;   /* sph_precision                                                  */
     int32_t use_graph;   /* 1: run the pass loop as a CUDA graph with a device-side loop  */
-    int32_t reserved;    /* must be 0                                                      */
+    int32_t list_entries;/* 0: none; 16..1024: keep cached neighbour lists.  Listing 1 loops
+                            over a neighbour list (ngblist) built by the search; the context
+                            keeps, for every particle, the particles its last search found
+                            within (1 + list_margin_pct / 100) h (at most list_entries of
+                            them, else no list), and a later pass of the same solve whose h
+                            stays within that radius evaluates the list instead of searching
+                            again.  Costs 4 * list_entries + 16 bytes of device memory per
+                            particle of capacity, allocated by sph_create; fixed for the
+                            context's lifetime.  The FP32 mode needs direct_pct = 0.        */
     const char *tune_cache; /* autotuner cache file, or NULL for built-in defaults         */
 } sph_params;
 
@@ -84,19 +92,22 @@ typedef struct {
     int64_t pair_evals;                      /* sum over passes of in-h pairs (self incl.) */
     double sort_ms;                          /* device time of the sort stage             */
     double solve_ms;                         /* device time of the solve                  */
-    double density_ms;                       /* device time inside the density kernels    */
-    int32_t density_launches;                /* density-kernel launches                   */
+    double density_ms;                       /* device time of the density stage of every
+                                                pass: cached-list evaluation, work-item
+                                                set-up and density kernels               */
+    int32_t density_launches;                /* passes whose density stage was timed      */
     int32_t pad;
     int64_t pair_tests;                      /* candidate-target distance tests performed */
     int64_t pairs_per_pass[SPH_MAX_PASSES];  /* in-h pairs of each pass                   */
     double density_ms_per_pass[SPH_MAX_PASSES]; /* density-kernel time of each pass       */
+    int64_t list_evals;                      /* target evaluations served by cached lists */
 } sph_stats;
 
 typedef struct sph_ctx sph_ctx;
 
 /* Knobs of the spatial decomposition and of the density kernels' launch, set by the
  * autotuner or by hand.  They change speed, never results beyond summation order.
- * Defaults: {0, 3, 1, 0, 0, 32, 256, 0}. */
+ * Defaults: {0, 3, 1, 0, 0, 32, 256, 0, 10}. */
 typedef struct {
     int32_t group_shift;  /* a work item gathers todo targets that share an octree cell of edge
                              >= h / 2^group_shift (-2..3)                                     */
@@ -117,6 +128,8 @@ typedef struct {
     int32_t block_threads;/* threads per block of the density kernels: 64, 128 or 256           */
     int32_t blocks_per_sm;/* resident blocks per SM of the persistent density grid, 0 = as many
                              as fit (occupancy); larger values are clamped to that              */
+    int32_t list_margin_pct; /* cached neighbour lists hold the particles within
+                             (1 + list_margin_pct / 100) h of the search (1..100)              */
 } sph_tuning;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
@@ -143,8 +156,9 @@ sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
  * order, read only) on the particles of the last sph_sort while it varies, one knob at a
  * time from the current tuning and keeping the best value of each (two rounds): the item
  * cap (0, 16, 32, 64), targets per item (8, 16, 32), the grouping level (group_shift
- * -1..1), the candidate cell size (cell_div 2..3), threads per block (128, 256) and
- * resident blocks per SM (all that fit, or one fewer).  Keeps the fastest tuning in the
+ * -1..1), the candidate cell size (cell_div 2..3), threads per block (128, 256),
+ * resident blocks per SM (all that fit, or one fewer) and, with cached lists, the list
+ * margin (5, 10, 20 %).  Keeps the fastest tuning in the
  * context and, when the context has a tune_cache file, appends it there; sph_sort applies
  * the last cached entry that matches the GPU, the particle-count bucket (floor log2 n),
  * periodic and precision.  best may be NULL.  Results never change beyond summation order.

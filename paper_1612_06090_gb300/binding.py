@@ -50,7 +50,7 @@ class SphParams(ctypes.Structure):
         ("max_iter", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("list_entries", ctypes.c_int32),
         ("tune_cache", ctypes.c_char_p),
     ]
 
@@ -71,6 +71,7 @@ class SphStats(ctypes.Structure):
         ("pair_tests", ctypes.c_int64),
         ("pairs_per_pass", ctypes.c_int64 * SPH_MAX_PASSES),
         ("density_ms_per_pass", ctypes.c_double * SPH_MAX_PASSES),
+        ("list_evals", ctypes.c_int64),
     ]
 
     def to_dict(self) -> dict:
@@ -89,6 +90,7 @@ class SphStats(ctypes.Structure):
             "pair_tests": int(self.pair_tests),
             "pairs_per_pass": [int(v) for v in self.pairs_per_pass[: max(0, min(p, SPH_MAX_PASSES))]],
             "density_ms_per_pass": [float(v) for v in self.density_ms_per_pass[: max(0, min(p, SPH_MAX_PASSES))]],
+            "list_evals": int(self.list_evals),
         }
 
 
@@ -102,6 +104,7 @@ class SphTuning(ctypes.Structure):
         ("item_max", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
+        ("list_margin_pct", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:
@@ -157,7 +160,7 @@ def lib() -> ctypes.CDLL:
 
 def make_params(box=(1.0, 1.0, 1.0), periodic=True, nngb=64.0, tol=2.0, max_iter=64,
                 precision=SPH_PREC_FP32_KAHAN, use_graph=False, kernel=SPH_KERNEL_M4,
-                tune_cache=None) -> SphParams:
+                tune_cache=None, list_entries=0) -> SphParams:
     p = SphParams()
     for d in range(3):
         p.box[d] = float(box[d])
@@ -168,7 +171,7 @@ def make_params(box=(1.0, 1.0, 1.0), periodic=True, nngb=64.0, tol=2.0, max_iter
     p.max_iter = int(max_iter)
     p.precision = int(precision)
     p.use_graph = int(bool(use_graph))
-    p.reserved = 0
+    p.list_entries = int(list_entries)
     p.tune_cache = tune_cache.encode() if tune_cache else None
     return p
 

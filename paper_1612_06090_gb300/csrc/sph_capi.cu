@@ -48,6 +48,8 @@ struct sph_ctx {
     int32_t *e_cnt = nullptr, *todo[2] = {nullptr, nullptr}, *flags = nullptr, *items = nullptr;
     int32_t *tsize = nullptr, *toff = nullptr;
     int32_t *nb_slot = nullptr;  // neighbour export: caller index -> sample row
+    int32_t *lst = nullptr, *lst_n = nullptr, *todo_s = nullptr;  // cached neighbour lists
+    double *lst_r = nullptr;
     float *h32 = nullptr, *e_rho32 = nullptr, *e_nw32 = nullptr, *e_dnw32 = nullptr;
     DevState *ds = nullptr;
 
@@ -70,7 +72,7 @@ struct sph_ctx {
         sph_tuning tuning{};
         KeyLayout kl{};
     } graph_key;
-    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0};
+    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0, 10};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
     int grid_cap = 0;
@@ -127,7 +129,8 @@ sph_status check_params(sph_ctx *c, const sph_params *p)
     if (p->max_iter < 1 || p->max_iter > SPH_MAX_PASSES)
         return fail(c, SPH_ERR_INVALID_ARG, "max_iter must be in [1, %d]", SPH_MAX_PASSES);
     if (p->use_graph != 0 && p->use_graph != 1) return fail(c, SPH_ERR_INVALID_ARG, "use_graph must be 0 or 1");
-    if (p->reserved != 0) return fail(c, SPH_ERR_INVALID_ARG, "reserved must be 0");
+    if (p->list_entries != 0 && (p->list_entries < 16 || p->list_entries > 1024))
+        return fail(c, SPH_ERR_INVALID_ARG, "list_entries must be 0 or in [16, 1024]");
     return SPH_OK;
 }
 
@@ -176,6 +179,11 @@ size_t carve(sph_ctx *c, char *base)
     c->tsize = (int32_t *)take((gcap + 1) * 4);
     c->toff = (int32_t *)take((gcap + 1) * 4);
     c->nb_slot = (int32_t *)take(cap * 4);
+    const int64_t le = c->params.list_entries;
+    c->lst = le > 0 ? (int32_t *)take((size_t)cap * (size_t)le * 4) : nullptr;
+    c->lst_n = le > 0 ? (int32_t *)take(cap * 4) : nullptr;
+    c->lst_r = le > 0 ? (double *)take(cap * 8) : nullptr;
+    c->todo_s = le > 0 ? (int32_t *)take(cap * 4) : nullptr;
     c->ds = (DevState *)take(sizeof(DevState));
     return off;
 }
@@ -247,6 +255,14 @@ SolveArgs solve_args(sph_ctx *c)
     }
     a.gmax = c->tuning.item_max;
     a.item_cap = c->tuning.item_cap;
+    // cached neighbour lists (the FP32 per-lane queue of direct_pct > 0 records none)
+    const bool lists = c->params.list_entries > 0 && (c->params.precision == SPH_PREC_FP64 || c->tuning.direct_pct == 0);
+    a.lst = lists ? c->lst : nullptr;
+    a.lst_n = c->lst_n;
+    a.lst_r = c->lst_r;
+    a.todo_s = c->todo_s;
+    a.list_entries = c->params.list_entries;
+    a.list_margin = 1.0f + (float)c->tuning.list_margin_pct * 0.01f;
     a.group_shift = c->tuning.group_shift;
     a.cell_div = c->tuning.cell_div;
     a.direct_pct = c->tuning.direct_pct;
@@ -266,7 +282,7 @@ int table_level(int64_t n, int lmax, int extra)
 }
 
 // Autotuner cache: one line per result,
-// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs" (the sph_tuning fields in
+// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs lm" (the sph_tuning fields in
 // order); the last matching line wins.
 std::string cache_key(const sph_ctx *c, int64_t n)
 {
@@ -287,8 +303,9 @@ bool cache_lookup(const sph_ctx *c, int64_t n, sph_tuning *t)
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
         sph_tuning x = c->tuning;
-        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra,
-                   &x.direct_pct, &x.item_cap, &x.item_max, &x.block_threads, &x.blocks_per_sm) == 9 &&
+        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra,
+                   &x.direct_pct, &x.item_cap, &x.item_max, &x.block_threads, &x.blocks_per_sm,
+                   &x.list_margin_pct) == 10 &&
             key == k) {
             *t = x;
             found = true;
@@ -303,8 +320,9 @@ void cache_store(const sph_ctx *c, int64_t n, const sph_tuning &t)
     if (c->tune_cache.empty()) return;
     FILE *f = fopen(c->tune_cache.c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div, t.table_extra,
-            t.direct_pct, t.item_cap, t.item_max, t.block_threads, t.blocks_per_sm);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div,
+            t.table_extra, t.direct_pct, t.item_cap, t.item_max, t.block_threads, t.blocks_per_sm,
+            t.list_margin_pct);
     fclose(f);
 }
 
@@ -315,7 +333,7 @@ bool tuning_ok(const sph_tuning *t)
            t->table_extra >= 0 && t->table_extra <= 1 && t->direct_pct >= 0 && t->direct_pct <= 101 &&
            (t->item_cap == 0 || (t->item_cap >= 2 && t->item_cap <= 64)) && pow2 &&
            (t->block_threads == 64 || t->block_threads == 128 || t->block_threads == 256) &&
-           t->blocks_per_sm >= 0 && t->blocks_per_sm <= 32;
+           t->blocks_per_sm >= 0 && t->blocks_per_sm <= 32 && t->list_margin_pct >= 1 && t->list_margin_pct <= 100;
 }
 
 sph_status read_state(sph_ctx *c)
@@ -466,6 +484,7 @@ sph_status run_solve(sph_ctx *c, double *h_inout, double *rho_out, int32_t *coun
         stats->exceeded = d.exceeded;
         stats->pair_evals = (int64_t)d.pair_evals;
         stats->pair_tests = (int64_t)d.pair_tests;
+        stats->list_evals = (int64_t)d.list_evals;
         for (int k = 0; k < SPH_MAX_PASSES; k++)
             stats->pairs_per_pass[k] = k < d.pass ? (int64_t)d.pairs_per_pass[k] : 0;
         float ms = 0.f;
@@ -585,6 +604,8 @@ sph_status sph_set_params(sph_ctx *ctx, const sph_params *params)
     if (!ctx) return SPH_ERR_INVALID_ARG;
     sph_status s = check_params(ctx, params);
     if (s != SPH_OK) return s;
+    if (params->list_entries != ctx->params.list_entries)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "list_entries is fixed when the context is created");
     const bool geometry_changed = params->periodic != ctx->params.periodic ||
                                   params->box[0] != ctx->params.box[0] ||
                                   params->box[1] != ctx->params.box[1] ||
@@ -757,8 +778,9 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
         return err;
     }
     const int mode = ctx->params.precision == SPH_PREC_FP64 ? 0 : 2;
+    const int nknobs = ctx->params.list_entries > 0 ? 7 : 6;
     for (int round = 0; round < 2; round++) {
-        for (int knob = 0; knob < 6; knob++) {
+        for (int knob = 0; knob < nknobs; knob++) {
             int vals[4];
             int nv = 0;
             switch (knob) {
@@ -767,6 +789,7 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
             case 2: vals[0] = -1, vals[1] = 0, vals[2] = 1, nv = 3; break;                 // group_shift
             case 3: vals[0] = 2, vals[1] = 3, nv = 2; break;                               // cell_div
             case 4: vals[0] = 128, vals[1] = 256, nv = 2; break;                           // block_threads
+            case 6: vals[0] = 5, vals[1] = 10, vals[2] = 20, nv = 3; break;                // list_margin_pct
             default: {                                                                     // blocks_per_sm
                 const int bt = best.block_threads;
                 const int ti = bt == 64 ? 0 : bt == 128 ? 1 : 2;
@@ -784,7 +807,8 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
                              : knob == 2 ? &t.group_shift
                              : knob == 3 ? &t.cell_div
                              : knob == 4 ? &t.block_threads
-                                         : &t.blocks_per_sm;
+                             : knob == 5 ? &t.blocks_per_sm
+                                         : &t.list_margin_pct;
                 if (*field == vals[v]) continue;
                 *field = vals[v];
                 const float ms = time_one(t, &err);
@@ -814,6 +838,7 @@ sph_status sph_density_eval(sph_ctx *ctx, const double *h_dev, double *rho_out_d
     if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
     cudaStream_t st = ctx->stream;
     SolveArgs a = solve_args(ctx);
+    a.lst = nullptr;  // one pass: nothing to reuse
     CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
     CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
     CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
@@ -845,6 +870,7 @@ sph_status sph_neighbours_sampled(sph_ctx *ctx, const double *h_dev, int64_t n_s
         return fail(ctx, SPH_ERR_UNSUPPORTED, "the neighbour export needs direct_pct = 0 in FP32");
     cudaStream_t st = ctx->stream;
     SolveArgs a = solve_args(ctx);
+    a.lst = nullptr;  // one pass, searched
     CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
     CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
     CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
@@ -886,6 +912,7 @@ sph_status sph_knn_solve(sph_ctx *ctx, int32_t k, double *h_inout_dev, double *r
     const int launches0 = ctx->launches;
     SolveArgs a = solve_args(ctx);
     a.free_first = 0;  // the density pass of leftover particles keeps the body under its test
+    a.lst = nullptr;
     CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
     CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
     CU(ctx, launch_knn_init(a, h_inout_dev, ctx->params.max_iter, k, st), "init");

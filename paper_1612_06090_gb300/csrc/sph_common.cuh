@@ -63,10 +63,12 @@ struct DevState {
     int32_t sort_status;       // input errors found by the sort (kept across solves)
     int32_t h_varies;          // some starting h differs from particle 0's (set by the solve init)
     int32_t free_now;          // this pass runs the branch-free FP32 pair loop
-    int32_t pad1;
+    int32_t dens_count;        // entries of this pass that the neighbour search evaluates (all of
+                               // them, or those without a usable cached neighbour list)
     unsigned long long pair_evals;  // in-h pairs accumulated over the solve
     unsigned long long pair_tests;  // candidate-target distance tests (work done, not counted
                                     // as algorithmic work)
+    unsigned long long list_evals;  // target evaluations served by cached neighbour lists
     int32_t todo_per_pass[kMaxPasses];
     unsigned long long pairs_per_pass[kMaxPasses];
 };

@@ -205,6 +205,10 @@ __device__ __forceinline__ void nb_record(const SolveArgs &a, int slot, int j)
     if (c < a.nb_max) a.nb_out[(int64_t)slot * a.nb_max + c] = a.idx[j];
 }
 
+// Auxiliary work of a density-kernel instantiation: none, the neighbour export of sampled
+// targets, or the recording of every target's cached neighbour list.
+constexpr int kAuxNone = 0, kAuxExport = 1, kAuxRecord = 2;
+
 // Per-lane geometry of the pair loop: lane = (target t, slice s); the lane tests staged
 // candidates s, s + slices, s + 2 slices, ... against target t.
 struct LaneTarget {
@@ -214,7 +218,17 @@ struct LaneTarget {
     int slices, s;
     int sh;            // log2(slices)
     int slot;          // neighbour export: sample row of the target, or -1
+    float r2l;         // list recording: squared list radius (FP64: widened); -1 for idle lanes
+    int tslot;         // list recording: the target's index in the item
+    int p;             // list recording: the target's sorted position
 };
+
+// List recording: a candidate (sorted position j) within the list radius of the lane's target.
+__device__ __forceinline__ void lst_record(const SolveArgs &a, int *lcnt, const LaneTarget &L, int j)
+{
+    const int c = atomicAdd(&lcnt[L.tslot], 1);
+    if (c < a.list_entries) a.lst[(int64_t)L.p * a.list_entries + c] = j;
+}
 
 // Stage layout of the packed FP32 path (kMode 2).  Candidate slot j is tested by slice
 // s = j mod S at step k = j / S (S = slices).  Steps 2i and 2i + 1 of one slice share two
@@ -265,15 +279,17 @@ __device__ __forceinline__ void shape32x2(float2 q, float2 &w, float2 &dw)
 // in-h pairs fall across the targets.
 // kMode: 0 = FP64 (queue), 1 = FP32 with the queue until the in-h share is known, 2 = FP32
 // evaluated directly (no queue, no ring memory).
-// kExp: also record the in-h candidates of sampled targets (neighbour export; sidx then holds
-// every staged candidate's sorted position in linear slot order).
-template <int kMode, int kKern, bool kExp>
+// kAux: kAuxExport also records the in-h candidates of sampled targets, kAuxRecord the
+// candidates within the list radius of every target (sidx then holds every staged candidate's
+// sorted position in linear slot order).
+template <int kMode, int kKern, int kAux>
 __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__restrict__ sidx,
                                       void *__restrict__ ring_raw, int cnt, int direct_pct,
                                       const LaneTarget &L,
                                       Acc32 &A32, Acc64 &A64, const double4_32a &ti, double h,
                                       double h2, const SegInfo &S,
-                                      const double4_32a *__restrict__ pdbl, const SolveArgs &a)
+                                      const double4_32a *__restrict__ pdbl, const SolveArgs &a,
+                                      int *__restrict__ lcnt)
 {
     constexpr bool kF64 = kMode == 0;
     constexpr bool kQueue = kMode < 2;
@@ -300,13 +316,19 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
                 const float2 dz = __fadd2_rn(f2(B.x, B.y), ntz);
                 const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
                 const bool in0 = r2.x < L.h2, in1 = r2.y < L.h2;
-                if constexpr (kExp) {
+                if constexpr (kAux == kAuxExport) {
                     if (L.slot >= 0) {
                         // slots of steps 2i and 2i + 1 of this lane's slice
                         const int j0 = ((2 * i) << L.sh) + L.s, j1 = j0 + (1 << L.sh);
                         if (in0 && j0 < cnt) nb_record(a, L.slot, sidx[j0]);
                         if (in1 && j1 < cnt) nb_record(a, L.slot, sidx[j1]);
                     }
+                }
+                if constexpr (kAux == kAuxRecord) {
+                    // padding candidates (3e18) are never within the list radius
+                    const int j0 = ((2 * i) << L.sh) + L.s, j1 = j0 + (1 << L.sh);
+                    if (r2.x < L.r2l) lst_record(a, lcnt, L, sidx[j0]);
+                    if (r2.y < L.r2l) lst_record(a, lcnt, L, sidx[j1]);
                 }
                 // kMode 2: the pair body runs when either candidate is within h, so a step in
                 // which no lane has one costs only the test; kMode 3: branch-free, the
@@ -342,7 +364,7 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
         if (kF64) {
             const int j = ring64[head & (kRing - 1)][lane];
             const bool in = pair64<kKern>(ti, pdbl[sidx[j]], h, h2, S, A64);
-            if (kExp && in && L.slot >= 0) nb_record(a, L.slot, sidx[j]);
+            if (kAux == kAuxExport && in && L.slot >= 0) nb_record(a, L.slot, sidx[j]);
         } else {
             pair32<kKern>(ring32[head & (kRing - 1)][lane], L.hinv2, A32);
         }
@@ -360,6 +382,7 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
             const float4 c = stage[j];
             const float dx = c.x - L.tx, dy = c.y - L.ty, dz = c.z - L.tz;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (kAux == kAuxRecord && r2 < L.r2l) lst_record(a, lcnt, L, sidx[j]);
             if (r2 < L.h2) {
                 if (kF64) ring64[tail & (kRing - 1)][lane] = j;
                 else ring32[tail & (kRing - 1)][lane] = make_float2(r2, c.w);
@@ -417,40 +440,44 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
 
 // Per-warp shared memory: the stage, the mode's queue memory, then the item's cell table
 // (exclusive prefix of the cell sizes and first particle of every cell).
-// The neighbour export (kExp) adds the staged candidates' sorted positions to the FP32 modes.
-template <int kMode, bool kExp = false>
+// The neighbour export and the list recording add the staged candidates' sorted positions to
+// the FP32 modes; the recording also keeps one counter per target of the item.
+template <int kMode, int kAux = kAuxNone>
 __host__ __device__ constexpr int warp_cell_offset()
 {
     return kStageCap * 16 + (kMode == 0   ? kStageCap * 4 + kRing * 32 * 4
                              : kMode == 1 ? kRing * 32 * 8
-                             : kExp       ? kStageCap * 4
+                             : kAux != 0  ? kStageCap * 4
                                           : 0);
 }
 
-template <int kMode, bool kExp = false>
+template <int kMode, int kAux = kAuxNone>
 __host__ __device__ constexpr int warp_smem_bytes()
 {
-    return warp_cell_offset<kMode, kExp>() + 2 * kMaxCells * 4;
+    return warp_cell_offset<kMode, kAux>() + 2 * kMaxCells * 4 + (kAux == kAuxRecord ? 32 * 4 : 0);
 }
 
-template <int kMode, int kKern, bool kExp = false>
+template <int kMode, int kKern, int kAux = kAuxNone>
 __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
     k_density(SolveArgs a, const int32_t *__restrict__ todo)
 {
     constexpr bool kF64 = kMode == 0;
+    constexpr bool kExp = kAux == kAuxExport;
+    constexpr bool kRec = kAux == kAuxRecord;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wbase = smem + (size_t)warp * warp_smem_bytes<kMode, kExp>();
+    unsigned char *wbase = smem + (size_t)warp * warp_smem_bytes<kMode, kAux>();
     float4 *stage = (float4 *)wbase;
     int *sidx = (int *)(wbase + kStageCap * 16);
     void *ring = wbase + kStageCap * 16 + (kF64 ? kStageCap * 4 : 0);
-    int *cpre = (int *)(wbase + warp_cell_offset<kMode, kExp>());
+    int *cpre = (int *)(wbase + warp_cell_offset<kMode, kAux>());
     int *cbeg = cpre + kMaxCells;
+    int *lcnt = cbeg + kMaxCells;  // list recording: candidates recorded per target of the item
     // the branched (2) and branch-free (3) FP32 kernels are both launched when the pass may use
     // either; the one the pass did not choose returns at once
     if (kMode >= 2 && a.free_first && (a.ds->free_now != 0) != (kMode == 3)) return;
     const int n_items = a.ds->n_items;
-    const int todo_count = a.ds->pass_count;
+    const int todo_count = a.ds->dens_count;
     const int pass = a.ds->pass;
     unsigned long long pairs = 0, tests = 0;
 
@@ -476,6 +503,8 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         const bool active = t < G;
         const int p = todo[t0 + (active ? t : 0)];
         L.slot = kExp && active ? a.nb_slot[a.idx[p]] : -1;
+        L.tslot = t;
+        L.p = p;
         const uint4 P = a.pfix[p];
         const double hd = kF64 ? a.h[p] : 0.0;
         const float hf = kF64 ? (float)hd : a.h32[p];
@@ -484,7 +513,12 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
 
         ItemGeom G3;
         int rel[3];
-        item_setup(S, a.kl, a.cell_div, active, P, hf, G3, rel);
+        // when recording lists, the staging region (box and ball) must hold every candidate
+        // within the list radius of every target, not only within its h
+        const float hq = !kRec ? hf
+                         : kF64 ? (float)(hd * (double)a.list_margin) * (1.0f + 1e-5f)
+                                : hf * a.list_margin * (1.0f + 1e-5f);
+        item_setup(S, a.kl, a.cell_div, active, P, hq, G3, rel);
         const float qf[3] = {(float)S.q[0], (float)S.q[1], (float)S.q[2]};
         // FP32 offsets are taken from the centre of the targets' box rather than the first
         // target: the largest offset a near-boundary pair needs is then half the box plus h,
@@ -533,8 +567,21 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
             const float hl = (float)(hd * (1.0 + 1e-4) + 4.0 * qmax);
             L.h2 = active ? hl * hl : -1.f;
             ti = a.pdbl[p];
+            if (kRec) {
+                const float rl = (float)(hd * a.list_margin * (1.0 + 1e-4) + 4.0 * qmax);
+                L.r2l = active ? rl * rl : -1.f;
+            }
         } else {
             L.h2 = active ? hf * hf : -1.f;
+            if (kRec) {
+                const float rl = hf * a.list_margin;
+                L.r2l = active ? rl * rl : -1.f;
+            }
+        }
+        if (kRec) {
+            __syncwarp();  // the previous item's counters have been read
+            if (active && L.s == 0) lcnt[t] = 0;
+            __syncwarp();
         }
 
         const int ncell = G3.nc[0] * G3.nc[1] * G3.nc[2];
@@ -613,13 +660,13 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
                     const int slot = cnt + __popc(m & lanemask_lt());
                     if (kMode >= 2) stage_pair_put((float *)stage, slot, L.sh, fx, fy, fz, __uint_as_float(Pj.w));
                     else stage[slot] = make_float4(fx, fy, fz, __uint_as_float(Pj.w));
-                    if (kF64 || kExp) sidx[slot] = j;
+                    if (kF64 || kAux != kAuxNone) sidx[slot] = j;
                 }
                 cnt += __popc(m);
                 if (cnt > kStage - 32) {
                     __syncwarp();
-                    flush<kMode, kKern, kExp>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd,
-                                              hd * hd, S, a.pdbl, a);
+                    flush<kMode, kKern, kAux>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd,
+                                              hd * hd, S, a.pdbl, a, lcnt);
                     staged += cnt;
                     cnt = 0;
                 }
@@ -627,8 +674,8 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
         }
         __syncwarp();
         if (cnt > 0) {
-            flush<kMode, kKern, kExp>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd,
-                                      S, a.pdbl, a);
+            flush<kMode, kKern, kAux>(stage, sidx, ring, cnt, a.direct_pct, L, A32, A64, ti, hd, hd * hd,
+                                      S, a.pdbl, a, lcnt);
             staged += cnt;
         }
 
@@ -686,6 +733,19 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
             }
         }
         if (lane == 0) tests += (unsigned long long)staged * (unsigned long long)G;
+        if (kRec) {
+            // a list holds every candidate within the list radius by the test above, so it serves
+            // any later h below that radius (with a margin for the rounding of that test)
+            __syncwarp();
+            if (active && L.s == 0) {
+                const int nrec = lcnt[t];
+                const bool fits = nrec <= a.list_entries;
+                a.lst_n[p] = fits ? nrec : -1;
+                a.lst_r[p] = fits ? (kF64 ? hd * (double)a.list_margin
+                                          : (double)(hf * a.list_margin) * (1.0 - 1e-5))
+                                  : 0.0;
+            }
+        }
     }
     pairs = warp_sum(pairs);
     if (lane == 0) {
@@ -697,6 +757,159 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
     }
 }
 
+
+// Cached-list pass: the todo targets whose recorded neighbour list still covers their h are
+// evaluated from that list, 8 lanes per target and 4 targets per warp; flags[t] = 1 marks the
+// targets that must search again (no list, or h beyond the list's radius).  Offsets come from
+// the exact 32-bit fixed-point differences of target and neighbour, rounded once to FP32 (FP64
+// mode: the FP64 pair exactly as the density pass forms it), so the in-h decisions and pair
+// terms are those of Eq. (1) on the list.
+constexpr int kListLanes = 8;
+constexpr int kListUnroll = 4;
+
+template <bool kF64, int kKern>
+__global__ void __launch_bounds__(kThreads) k_list_eval(SolveArgs a, const int32_t *__restrict__ todo)
+{
+    const int T = a.ds->pass_count;
+    const int pass = a.ds->pass;
+    const int lane = lane_id(), sub = lane & (kListLanes - 1);
+    const int gw = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
+    constexpr int kPerWarp = 32 / kListLanes;
+    unsigned long long pairs = 0, tests = 0, served = 0;
+    for (int tb = gw * kPerWarp; tb < T; tb += nw * kPerWarp) {
+        const int t = tb + lane / kListLanes;
+        const bool have = t < T;
+        const int p = have ? todo[t] : 0;
+        const double hd = a.h[p];
+        const int ln = have ? a.lst_n[p] : -1;
+        const bool use = have && ln >= 0 && hd <= a.lst_r[p];
+        if (have && sub == 0) a.flags[t] = use ? 0 : 1;
+        const int nl = use ? ln : 0;
+        const int nmax = __reduce_max_sync(kFull, nl);
+        if (nmax == 0) continue;
+        const uint4 P = a.pfix[p];
+        const int g = a.kl.seg_bits > 0 ? (int)(a.key[p] >> (3 * a.kl.lmax)) : 0;
+        const SegInfo &S = a.segs[g];
+        const float qx = (float)S.q[0], qy = (float)S.q[1], qz = (float)S.q[2];
+        const float hf = kF64 ? (float)hd : a.h32[p];
+        const float h2 = hf * hf, hinv2 = 1.0f / (hf * hf);
+        const double4_32a ti = kF64 ? a.pdbl[p] : make_double4_32a(0, 0, 0, 0);
+        const double hd2 = hd * hd;
+        const int32_t *lst = a.lst + (int64_t)p * a.list_entries;
+        Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        Acc64 A64 = {0.0, 0.0, 0.0, 0};
+        int since = 0;
+        for (int k0 = 0; k0 < nmax; k0 += kListLanes * kListUnroll) {
+            // the list entries first, then their records, all independent loads
+            int jj[kListUnroll];
+#pragma unroll
+            for (int u = 0; u < kListUnroll; u++) {
+                const int k = k0 + kListLanes * u + sub;
+                jj[u] = k < nl ? lst[k] : -1;
+            }
+            if constexpr (kF64) {
+                double4_32a C[kListUnroll];
+#pragma unroll
+                for (int u = 0; u < kListUnroll; u++) C[u] = a.pdbl[jj[u] >= 0 ? jj[u] : p];
+#pragma unroll
+                for (int u = 0; u < kListUnroll; u++)
+                    if (jj[u] >= 0) pair64<kKern>(ti, C[u], hd, hd2, S, A64);
+            } else {
+                uint4 C[kListUnroll];
+#pragma unroll
+                for (int u = 0; u < kListUnroll; u++) C[u] = a.pfix[jj[u] >= 0 ? jj[u] : p];
+#pragma unroll
+                for (int u = 0; u < kListUnroll; u++) {
+                    if (jj[u] < 0) continue;
+                    const float dx = (float)(int32_t)(C[u].x - P.x) * qx;
+                    const float dy = (float)(int32_t)(C[u].y - P.y) * qy;
+                    const float dz = (float)(int32_t)(C[u].z - P.z) * qz;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (r2 < h2) {
+                        const float q = sqrt_approx(r2 * hinv2);
+                        float w, dw;
+                        shape32<kKern, true>(q, w, dw);
+                        A32.p_mw = fmaf(__uint_as_float(C[u].w), w, A32.p_mw);
+                        A32.p_w += w;
+                        A32.p_dw += dw;
+                        A32.count++;
+                    }
+                }
+                // at most 32 terms per partial sum, as in the density pass
+                if (++since == 32 / kListUnroll) {
+                    merge32(A32);
+                    since = 0;
+                }
+            }
+        }
+        if (use && sub == 0) {
+            tests += (unsigned long long)ln;
+            served++;
+        }
+        // combine the 8 lanes of each target
+        int count = kF64 ? A64.count : A32.count;
+        if constexpr (kF64) {
+            double smw = A64.s_mw, sw = A64.s_w, sdw = A64.s_dw;
+#pragma unroll
+            for (int o = kListLanes / 2; o > 0; o >>= 1) {
+                smw += __shfl_xor_sync(kFull, smw, o);
+                sw += __shfl_xor_sync(kFull, sw, o);
+                sdw += __shfl_xor_sync(kFull, sdw, o);
+                count += __shfl_xor_sync(kFull, count, o);
+            }
+            if (use && sub == 0) {
+                const double h = hd;
+                if (kKern == 0) {
+                    a.e_rho[p] = smw * (8.0 / (kPi * h * h * h));
+                    a.e_nw[p] = (32.0 / 3.0) * sw;
+                    a.e_dnw[p] = (32.0 / 3.0) * sdw / h;
+                } else {
+                    a.e_rho[p] = smw * (1365.0 / (64.0 * kPi * h * h * h));
+                    a.e_nw[p] = (1365.0 / 48.0) * sw;
+                    a.e_dnw[p] = (1365.0 / 48.0) * sdw / h;
+                }
+                a.e_cnt[p] = count;
+                pairs += (unsigned long long)count;
+            }
+        } else {
+            merge32(A32);
+            float smw = A32.s_mw, cmw = A32.c_mw, sw = A32.s_w, cw = A32.c_w, sdw = A32.s_dw, cdw = A32.c_dw;
+#pragma unroll
+            for (int o = kListLanes / 2; o > 0; o >>= 1) {
+                smw += __shfl_xor_sync(kFull, smw, o);
+                cmw += __shfl_xor_sync(kFull, cmw, o);
+                sw += __shfl_xor_sync(kFull, sw, o);
+                cw += __shfl_xor_sync(kFull, cw, o);
+                sdw += __shfl_xor_sync(kFull, sdw, o);
+                cdw += __shfl_xor_sync(kFull, cdw, o);
+                count += __shfl_xor_sync(kFull, count, o);
+            }
+            if (use && sub == 0) {
+                const float hi = 1.0f / hf;
+                const float crho = kKern == 0 ? 2.0f * 2.546479089f : 6.788953041f;
+                const float cnw = kKern == 0 ? 2.0f * 10.66666667f : 28.4375f;
+                const float cdnw = kKern == 0 ? 6.0f * 10.66666667f : 22.0f * 28.4375f;
+                a.e_rho32[p] = crho * (hi * hi * hi) * (smw - cmw);
+                a.e_nw32[p] = cnw * (sw - cw);
+                a.e_dnw32[p] = cdnw * hi * (sdw - cdw);
+                a.e_cnt[p] = count;
+                pairs += (unsigned long long)count;
+            }
+        }
+    }
+    pairs = warp_sum(pairs);
+    tests = warp_sum(tests);
+    served = warp_sum(served);
+    if (lane == 0) {
+        if (pairs) {
+            atomicAdd(&a.ds->pair_evals, pairs);
+            if (pass < kMaxPasses) atomicAdd(&a.ds->pairs_per_pass[pass], pairs);
+        }
+        if (tests) atomicAdd(&a.ds->pair_tests, tests);
+        if (served) atomicAdd(&a.ds->list_evals, served);
+    }
+}
 
 }  // namespace
 
@@ -733,37 +946,61 @@ int density_blocks_per_sm(int precision, int direct_pct, int threads)
     }
 }
 
-template <int kMode, bool kExp = false>
+template <int kMode, int kAux = kAuxNone>
 void launch_mode(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
     const int threads = (a.block_threads == 64 || a.block_threads == 128) ? a.block_threads : kThreads;
-    const int bytes = (threads / 32) * warp_smem_bytes<kMode, kExp>();
-    if (kExp) {
-        // the export instantiations are not prepared by density_blocks_per_sm; the persistent
+    const int bytes = (threads / 32) * warp_smem_bytes<kMode, kAux>();
+    if (kAux != kAuxNone) {
+        // the auxiliary instantiations are not prepared by density_blocks_per_sm; the persistent
         // grid stays correct whatever number of its blocks are resident at once
-        cudaFuncSetAttribute(k_density<kMode, 0, kExp>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        cudaFuncSetAttribute(k_density<kMode, 1, kExp>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_density<kMode, 0, kAux>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kWarps * warp_smem_bytes<kMode, kAux>());
+        cudaFuncSetAttribute(k_density<kMode, 1, kAux>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kWarps * warp_smem_bytes<kMode, kAux>());
     }
-    if (a.kernel == 0) k_density<kMode, 0, kExp><<<a.density_grid, threads, bytes, st>>>(a, todo);
-    else k_density<kMode, 1, kExp><<<a.density_grid, threads, bytes, st>>>(a, todo);
+    if (a.kernel == 0) k_density<kMode, 0, kAux><<<a.density_grid, threads, bytes, st>>>(a, todo);
+    else k_density<kMode, 1, kAux><<<a.density_grid, threads, bytes, st>>>(a, todo);
+}
+
+template <int kAux>
+void launch_modes(const SolveArgs &a, const int32_t *todo, int mode, cudaStream_t st)
+{
+    if (mode == 0) {
+        launch_mode<0, kAux>(a, todo, st);
+    } else {
+        if (a.free_first) {
+            launch_mode<3, kAux>(a, todo, st);
+            if (a.launches) *a.launches += 1;
+        }
+        launch_mode<2, kAux>(a, todo, st);
+    }
+}
+
+cudaError_t launch_list_eval(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
+{
+    constexpr int per_block = kThreads / 32 * (32 / kListLanes);
+    int64_t blocks = (a.n + per_block - 1) / per_block;
+    if (blocks > a.grid_cap) blocks = a.grid_cap;
+    if (blocks < 1) blocks = 1;
+    const bool f64 = a.precision == 0;
+    if (f64 && a.kernel == 0) k_list_eval<true, 0><<<(int)blocks, kThreads, 0, st>>>(a, todo);
+    else if (f64) k_list_eval<true, 1><<<(int)blocks, kThreads, 0, st>>>(a, todo);
+    else if (a.kernel == 0) k_list_eval<false, 0><<<(int)blocks, kThreads, 0, st>>>(a, todo);
+    else k_list_eval<false, 1><<<(int)blocks, kThreads, 0, st>>>(a, todo);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
 {
     const int mode = mode_of(a.precision, a.direct_pct);
-    if (a.nb_out) {
-        // neighbour export (test aid): the same pass with the recording instantiations; the
-        // per-lane queue of the non-default FP32 mode 1 has no export
+    if (a.nb_out || a.lst) {
+        // the neighbour export (test aid) and the list recording run the same pass in their own
+        // instantiations; the per-lane queue of the non-default FP32 mode 1 has neither
         if (mode == 1) return cudaErrorNotSupported;
-        if (mode == 0) {
-            launch_mode<0, true>(a, todo, st);
-        } else {
-            if (a.free_first) {
-                launch_mode<3, true>(a, todo, st);
-                if (a.launches) *a.launches += 1;
-            }
-            launch_mode<2, true>(a, todo, st);
-        }
+        if (a.nb_out) launch_modes<kAuxExport>(a, todo, mode, st);
+        else launch_modes<kAuxRecord>(a, todo, mode, st);
         if (a.launches) *a.launches += 1;
         return cudaGetLastError();
     }

@@ -89,6 +89,18 @@ struct SolveArgs {
     int32_t *nb_out;
     int32_t *nb_cnt;
     int nb_max;
+    // cached neighbour lists (lst == nullptr: off).  A neighbour search records, for each of its
+    // targets p, the sorted positions of the particles within list_margin * h_p (at most
+    // list_entries) in lst[p * list_entries ..], their number in lst_n[p] (-1: no list) and the
+    // radius every h up to which the list serves in lst_r[p]; a later pass of the same solve whose
+    // h stays within lst_r evaluates the list instead of searching (targets that search go
+    // through todo_s)
+    int32_t *lst;
+    int32_t *lst_n;
+    double *lst_r;
+    int32_t *todo_s;
+    int list_entries;
+    float list_margin;         // > 1
 };
 
 cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_iter, cudaStream_t st);
@@ -101,6 +113,8 @@ cudaError_t launch_scatter(const SolveArgs &a, double *h_out, double *rho_out, i
 
 // sph_density.cu
 cudaError_t launch_density(const SolveArgs &a, const int32_t *todo, cudaStream_t st);
+// evaluate the todo targets whose cached lists still cover their h; flags[t] = 1 for the others
+cudaError_t launch_list_eval(const SolveArgs &a, const int32_t *todo, cudaStream_t st);
 // resident blocks per SM of the density kernel of this precision / mode at this block size
 int density_blocks_per_sm(int precision, int direct_pct, int block_threads = 256);
 // k-nearest-neighbour pass over todo (one warp per target): selects h for targets whose

@@ -48,9 +48,11 @@ __device__ __forceinline__ float expected_neighbours(uint64_t k, float h, const 
     return (float)cnt / vol * (4.18879020f * h * h * h);
 }
 
+// hmul >= 1 scales h for the single-target test only (the list radius when lists are recorded).
 __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
                                           const KeyLayout &kl, int shift, int &lvl,
-                                          uint64_t &prefix, bool &big, const int32_t *ctab)
+                                          uint64_t &prefix, bool &big, const int32_t *ctab,
+                                          float hmul = 1.0f)
 {
     const int cb = kl.coord_bits;
     const float maxinv = (float)fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
@@ -64,7 +66,8 @@ __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
     if (ctab && l >= 2 && expected_neighbours(k, h, S, kl, ctab) < 16.f) l -= 2;
     lvl = l;
     prefix = k >> (3 * (kl.lmax - l));
-    big = S.periodic && ((float)(1ll << (cb - l)) + hu >= (float)(1ll << (cb - 1)));
+    const float hb = hmul > 1.0f ? fminf(ceilf(h * hmul * maxinv * (1.0f + 1.0f / 1048576.0f)) + 1.0f, 1e30f) : hu;
+    big = S.periodic && ((float)(1ll << (cb - l)) + hb >= (float)(1ll << (cb - 1)));
 }
 
 __device__ void reset_state(DevState *ds, int64_t n, int max_iter)
@@ -80,6 +83,7 @@ __device__ void reset_state(DevState *ds, int64_t n, int max_iter)
     ds->pass_count = 0;
     ds->pair_evals = 0ull;
     ds->pair_tests = 0ull;
+    ds->list_evals = 0ull;
     for (int k = 0; k < kMaxPasses; k++) {
         ds->todo_per_pass[k] = 0;
         ds->pairs_per_pass[k] = 0ull;
@@ -104,6 +108,7 @@ __global__ void k_solve_init(SolveArgs a, const double *__restrict__ h_in, int m
         a.hhi[p] = HUGE_VAL;
         a.e_h[p] = hv;
         a.todo[0][p] = (int32_t)p;
+        if (a.lst) a.lst_n[p] = -1;  // lists belong to one solve
     }
     if (bad) atomicOr(&a.ds->status, bad);
     if (varies) atomicOr(&a.ds->h_varies, 1);  // cleared by the host before this kernel
@@ -168,6 +173,7 @@ __global__ void k_pass_begin(DevState *ds, int free_first)
     ds->todo_next = 0;
     const bool run = ds->todo_count > 0 && ds->pass < ds->max_iter;
     ds->pass_count = run ? ds->todo_count : 0;
+    ds->dens_count = ds->pass_count;  // with cached lists, replaced by the entries that search
     ds->free_now = free_first && ds->pass == 0 && !ds->h_varies;
     if (run && ds->pass < kMaxPasses) ds->todo_per_pass[ds->pass] = ds->todo_count;
 }
@@ -196,7 +202,7 @@ __global__ void k_set_loop(cudaGraphConditionalHandle handle, const DevState *ds
 // The item's query box uses the targets' actual bounds, so the rule only steers efficiency.
 __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
 {
-    const int T = a.ds->pass_count;
+    const int T = a.ds->dens_count;
     const bool dense = 8 * (int64_t)T >= a.n;
     // the sparse-target rule: first pass of batched open groups (isolated halo particles)
     const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
@@ -206,7 +212,8 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
         int l;
         uint64_t pre;
         bool big;
-        bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big, ctab0);
+        const float hmul = a.lst ? a.list_margin * 1.001f : 1.0f;
+        bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big, ctab0, hmul);
         int head = (t % a.gmax == 0) || big;
         if (!head) {
             const int pp = todo[t - 1];
@@ -214,7 +221,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
             int lp;
             uint64_t prep;
             bool bigp;
-            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp, ctab0);
+            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp, ctab0, hmul);
             if (dense) {
                 const int m = lp < l ? lp : l;
                 head = bigp || (l - lp > 1) || (lp - l > 1) ||
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
     constexpr int kHalo = kCapMax + 2;
     __shared__ uint64_t sk[kCapTile + 2 * kHalo];
     __shared__ int sl[kCapTile + 1];  // entries base - 1 .. base + kCapTile - 1: level | big << 8
-    const int T = a.ds->pass_count;
+    const int T = a.ds->dens_count;
     const int cap = a.item_cap < kCapMax ? a.item_cap : kCapMax;
     const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
     const int ntiles = (T + kCapTile - 1) / kCapTile;
@@ -285,7 +292,8 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
             int lh;
             uint64_t pre;
             bool big;
-            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, lh, pre, big, ctab0);
+            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, lh, pre, big, ctab0,
+                      a.lst ? a.list_margin * 1.001f : 1.0f);
             if (big) return lh | (1 << 8);
             const int nl = a.kl.lmax - lh + 1 < kCapLevels ? a.kl.lmax - lh + 1 : kCapLevels;
             // back[k]: entries from the start of the level-(lh + k) run to t inclusive;
@@ -470,15 +478,28 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
     const int32_t *todo = a.todo[cur];
     const int grid = blocks_for(a.n, a.grid_cap);
     k_pass_begin<<<1, 1, 0, st>>>(a.ds, a.free_first);
-    if (a.item_cap > 0) k_item_flags_capped<<<grid, kCapTile, 0, st>>>(a, todo);
-    else k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
-    if (a.launches) *a.launches += 2;
-    // item starts = positions of the head flags
-    cudaError_t e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->pass_count,
-                                &a.ds->n_items, a.scan_aux, a.grid_cap, st, a.launches);
-    if (e != cudaSuccess) return e;
+    if (a.launches) *a.launches += 1;
+    cudaError_t e = cudaSuccess;
     if (a.dens_ev[0]) cudaEventRecord(a.dens_ev[0], st);
-    e = launch_density(a, todo, st);
+    // with cached lists: the targets whose list still covers their h are evaluated from it, the
+    // others (flags) go on to the neighbour search through todo_s
+    const int32_t *stodo = todo;
+    if (a.lst) {
+        e = launch_list_eval(a, todo, st);
+        if (e != cudaSuccess) return e;
+        e = compact_i32(a.flags, todo, a.todo_s, nullptr, a.n, &a.ds->pass_count, &a.ds->dens_count,
+                        a.scan_aux, a.grid_cap, st, a.launches);
+        if (e != cudaSuccess) return e;
+        stodo = a.todo_s;
+    }
+    if (a.item_cap > 0) k_item_flags_capped<<<grid, kCapTile, 0, st>>>(a, stodo);
+    else k_item_flags<<<grid, kThreads, 0, st>>>(a, stodo);
+    if (a.launches) *a.launches += 1;
+    // item starts = positions of the head flags
+    e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->dens_count, &a.ds->n_items, a.scan_aux,
+                    a.grid_cap, st, a.launches);
+    if (e != cudaSuccess) return e;
+    e = launch_density(a, stodo, st);
     if (e != cudaSuccess) return e;
     if (a.dens_ev[1]) cudaEventRecord(a.dens_ev[1], st);
     if (!update) return cudaGetLastError();

@@ -110,6 +110,9 @@ def test_create_rejects_bad_arguments_on_the_host(B):
         dict(box=(1.0, 0.0, 1.0)),
         dict(box=(1.0, float("inf"), 1.0)),
         dict(precision=7),
+        dict(list_entries=8),       # cached lists hold 16..1024 entries
+        dict(list_entries=2000),
+        dict(list_entries=-1),
     ]
     for kw in cases:
         st, ctx = B.sph_create(B.make_params(**kw), 100)
