@@ -144,7 +144,9 @@ typedef struct {
 sph_status sph_create(const sph_params *params, int64_t capacity, void *cuda_stream, sph_ctx **out);
 
 /* Replace the solve parameters of a context (precision, nngb, tol, max_iter, use_graph).
- * Changing box or periodic invalidates the sorted state (sph_sort must run again). */
+ * Changing box or periodic invalidates the sorted state (sph_sort must run again), and so
+ * does switching to FP64 after a sort in FP32 (an FP32 sort keeps no FP64 records).  The
+ * list_entries of a context cannot change (INVALID_ARG). */
 sph_status sph_set_params(sph_ctx *ctx, const sph_params *params);
 
 /* Read or replace the tuning of a context.  Errors: INVALID_ARG (NULL, out of range). */
@@ -166,7 +168,8 @@ sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
 sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best);
 
 /* Spatially order n particles (Morton keys on 32-bit fixed-point coordinates, radix
- * sort, gather into a sorted SoA, cell tables).  This is the spatial structure behind the
+ * sort, gather into a sorted SoA, cell tables; in FP32 the gather moves only the 16-byte
+ * fixed-point records, in FP64 also the FP64 ones).  This is the spatial structure behind the
  * neighbour search: the paper's Barnes-Hut tree stored as a flat array (Sec. II-A), here an
  * octree implicit in the Morton order, and its AoS-to-SoA gather (Sec. IV-B).  The gather
  * keeps only the fields the density loop reads.  pos_xyz_dev holds three planes of n

@@ -29,6 +29,7 @@ struct sph_ctx {
 
     // sorted state
     bool sorted = false;
+    bool fp64_records = false;  // the sort filled the FP64 records (an FP64 sort)
     int64_t n = 0;
     KeyLayout kl{};
     int which = 0;  // key/idx buffer holding the sorted order
@@ -609,7 +610,9 @@ sph_status sph_set_params(sph_ctx *ctx, const sph_params *params)
     const bool geometry_changed = params->periodic != ctx->params.periodic ||
                                   params->box[0] != ctx->params.box[0] ||
                                   params->box[1] != ctx->params.box[1] ||
-                                  params->box[2] != ctx->params.box[2];
+                                  params->box[2] != ctx->params.box[2] ||
+                                  // an FP32 sort keeps no FP64 records
+                                  (params->precision == SPH_PREC_FP64 && !ctx->fp64_records);
     ctx->params = *params;
     ctx->tune_cache = params->tune_cache ? params->tune_cache : "";
     ctx->params.tune_cache = nullptr;
@@ -653,9 +656,13 @@ sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const do
         if (cache_lookup(ctx, n, &cached) && tuning_ok(&cached)) ctx->tuning = cached;
     }
     ctx->n = n;
-    ctx->kl.lmax = 21;
+    // 16 octree levels (cells down to 2^-16 of the box) in 48-bit keys: six radix passes.  The
+    // grouping and enumeration levels never go finer than the key (only a cell's candidate count,
+    // not the result, depends on it), and no work item needs cells that fine unless h is below
+    // about 1e-5 of the box.
+    ctx->kl.lmax = 16;
     ctx->kl.seg_bits = 0;
-    ctx->kl.key_bits = 63;
+    ctx->kl.key_bits = 48;
     ctx->kl.coord_bits = 32;
     SegInfo &sg = ctx->seg_host;
     memset(&sg, 0, sizeof(sg));
@@ -680,11 +687,20 @@ sph_status sph_sort(sph_ctx *ctx, int64_t n, const double *pos_xyz_dev, const do
     CU(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevState), st), "clearing the device state");
     const int launches0 = ctx->launches;
     SortArgs a = sort_args(ctx);
-    CU(ctx, launch_keys_periodic(a, n, pos_xyz_dev, mass_dev, sg, p.box, st), "morton keys");
+    // FP32 solves read only the fixed-point records: the key kernel leaves them in caller order in
+    // the FP64 records' memory and the gather moves one record per particle; an FP64 sort gathers
+    // both from the caller's arrays
+    const bool fp64 = p.precision == SPH_PREC_FP64;
+    uint4 *rec = fp64 ? nullptr : (uint4 *)ctx->pdbl;
+    CU(ctx, launch_keys_periodic(a, n, pos_xyz_dev, mass_dev, sg, p.box, st, rec), "morton keys");
     int which = 0;
     CU(ctx, launch_radix_sort(a, n, &which, st), "radix sort");
     ctx->which = which;
-    CU(ctx, launch_gather_periodic(a, n, pos_xyz_dev, mass_dev, ctx->idx[which], sg, st), "gather");
+    if (fp64)
+        CU(ctx, launch_gather_periodic(a, n, pos_xyz_dev, mass_dev, ctx->idx[which], sg, st), "gather");
+    else
+        CU(ctx, launch_gather_rec(a, n, ctx->idx[which], rec, st), "gather");
+    ctx->fp64_records = fp64;
     CU(ctx, launch_cell_table(a, n, ctx->key[which], st), "cell table");
     CU(ctx, cudaEventRecord(ctx->ev[1], st), "event");
     ctx->sort_launches = ctx->launches - launches0;
@@ -1025,11 +1041,17 @@ sph_status sph_batch_solve(sph_ctx *ctx, int64_t n_groups, const int64_t *offset
     CU(ctx, launch_group_setup(a, n_groups, offsets_dev, pos_xyz_dev, n, nngb_dev, tol_dev, ctx->tsize,
                                ctx->toff, st),
        "group setup");
-    CU(ctx, launch_keys_open(a, n, pos_xyz_dev, mass_dev, offsets_dev, n_groups, st), "morton keys");
+    const bool fp64 = ctx->params.precision == SPH_PREC_FP64;
+    uint4 *rec = fp64 ? nullptr : (uint4 *)ctx->pdbl;
+    CU(ctx, launch_keys_open(a, n, pos_xyz_dev, mass_dev, offsets_dev, n_groups, st, rec), "morton keys");
     int which = 0;
     CU(ctx, launch_radix_sort(a, n, &which, st), "radix sort");
     ctx->which = which;
-    CU(ctx, launch_gather_open(a, n, pos_xyz_dev, mass_dev, ctx->idx[which], ctx->key[which], st), "gather");
+    if (fp64)
+        CU(ctx, launch_gather_open(a, n, pos_xyz_dev, mass_dev, ctx->idx[which], ctx->key[which], st), "gather");
+    else
+        CU(ctx, launch_gather_rec(a, n, ctx->idx[which], rec, st), "gather");
+    ctx->fp64_records = fp64;
     CU(ctx, launch_cell_table(a, n, ctx->key[which], st), "cell table");
     CU(ctx, cudaEventRecord(ctx->ev[1], st), "event");
     ctx->sort_launches = ctx->launches - launches0;

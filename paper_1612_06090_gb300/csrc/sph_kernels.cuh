@@ -25,19 +25,25 @@ struct SortArgs {
 };
 
 int64_t radix_hist_size(int64_t n_max);
+// rec (nullable): caller-order fixed-point records for launch_gather_rec (FP32 sorts)
 cudaError_t launch_keys_periodic(const SortArgs &a, int64_t n, const double *pos, const double *mass,
-                                 const SegInfo &seg, const double box[3], cudaStream_t st);
+                                 const SegInfo &seg, const double box[3], cudaStream_t st,
+                                 uint4 *rec = nullptr);
 cudaError_t launch_group_setup(const SortArgs &a, int64_t n_groups, const int64_t *offsets,
                                const double *pos, int64_t n, const double *nngb, const double *tol,
                                int32_t *tsize, int32_t *toff, cudaStream_t st);
 cudaError_t launch_keys_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
-                             const int64_t *offsets, int64_t n_groups, cudaStream_t st);
+                             const int64_t *offsets, int64_t n_groups, cudaStream_t st,
+                             uint4 *rec = nullptr);
 cudaError_t launch_radix_sort(const SortArgs &a, int64_t n, int *which, cudaStream_t st);
 cudaError_t launch_gather_periodic(const SortArgs &a, int64_t n, const double *pos,
                                    const double *mass, const int32_t *idx, const SegInfo &seg,
                                    cudaStream_t st);
 cudaError_t launch_gather_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
                                const int32_t *idx, const uint64_t *key, cudaStream_t st);
+// pfix[p] = rec[idx[p]]: the sorted fixed-point records without the FP64 ones
+cudaError_t launch_gather_rec(const SortArgs &a, int64_t n, const int32_t *idx, const uint4 *rec,
+                              cudaStream_t st);
 cudaError_t launch_cell_table(const SortArgs &a, int64_t n, const uint64_t *key, cudaStream_t st);
 
 // Buffers and state of the solve.

@@ -48,6 +48,13 @@ __device__ __forceinline__ float expected_neighbours(uint64_t k, float h, const 
     return (float)cnt / vol * (4.18879020f * h * h * h);
 }
 
+// Smallest e with 2^e >= x, for a positive normal float x (exact, from the exponent bits).
+__device__ __forceinline__ int ceil_log2f(float x)
+{
+    const int b = __float_as_int(x);
+    return ((b >> 23) & 0xff) - 127 + ((b & 0x7fffff) != 0 ? 1 : 0);
+}
+
 // hmul >= 1 scales h for the single-target test only (the list radius when lists are recorded).
 __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
                                           const KeyLayout &kl, int shift, int &lvl,
@@ -58,8 +65,9 @@ __device__ __forceinline__ void bucket_of(uint64_t k, float h, const SegInfo &S,
     const float maxinv = (float)fmax(S.inv_q[0], fmax(S.inv_q[1], S.inv_q[2]));
     const float hu = fminf(ceilf(h * maxinv * (1.0f + 1.0f / 1048576.0f)) + 1.0f, 1e30f);
     const float edge = ldexpf(hu, -shift);
-    int l = kl.lmax;
-    while (l > 0 && (float)(1ll << (cb - l)) < edge) l--;
+    // the finest level l <= lmax whose cell edge 2^(cb - l) is at least edge (0 if none)
+    int l = cb - ceil_log2f(edge);
+    l = l > kl.lmax ? kl.lmax : l < 0 ? 0 : l;
     // ctab given (first pass of batched groups): a target whose starting h holds few neighbours
     // groups two levels coarser, so neighbouring isolated targets share items instead of paying
     // an item each (the todo list is still complete there, so consecutive targets are neighbours)
@@ -206,22 +214,33 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
     const bool dense = 8 * (int64_t)T >= a.n;
     // the sparse-target rule: first pass of batched open groups (isolated halo particles)
     const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-        const int p = todo[t];
-        const uint64_t k = a.key[p];
-        int l;
-        uint64_t pre;
-        bool big;
-        const float hmul = a.lst ? a.list_margin * 1.001f : 1.0f;
-        bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big, ctab0, hmul);
+    const float hmul = a.lst ? a.list_margin * 1.001f : 1.0f;
+    const int lane = threadIdx.x & 31;
+    // lanes hold consecutive entries, so an entry's predecessor is the previous lane's entry
+    // (lane 0 works its own out); the loop bound is the warp's first entry, so shuffles see the
+    // whole warp
+    for (int tb = blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < T; tb += gridDim.x * blockDim.x) {
+        const int t = tb + lane;
+        const bool have = t < T;
+        uint64_t k = 0, pre = 0;
+        int l = 0;
+        bool big = false;
+        if (have) {
+            const int p = todo[t];
+            k = a.key[p];
+            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big, ctab0, hmul);
+        }
+        uint64_t kp = __shfl_up_sync(kFull, k, 1), prep = __shfl_up_sync(kFull, pre, 1);
+        int lp = __shfl_up_sync(kFull, l, 1);
+        bool bigp = __shfl_up_sync(kFull, (int)big, 1) != 0;
+        if (lane == 0 && have && t > 0) {
+            const int pp = todo[t - 1];
+            kp = a.key[pp];
+            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp, ctab0, hmul);
+        }
+        if (!have) continue;
         int head = (t % a.gmax == 0) || big;
         if (!head) {
-            const int pp = todo[t - 1];
-            const uint64_t kp = a.key[pp];
-            int lp;
-            uint64_t prep;
-            bool bigp;
-            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp, ctab0, hmul);
             if (dense) {
                 const int m = lp < l ? lp : l;
                 head = bigp || (l - lp > 1) || (lp - l > 1) ||

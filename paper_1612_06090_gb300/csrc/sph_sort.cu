@@ -64,11 +64,14 @@ __device__ __forceinline__ bool finite_bits(double x)
     return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) <= 0x7fefffffffffffffull;
 }
 
+// rec (nullable): the particle's 16-byte fixed-point record {X, Y, Z, FP32 mass}, written in
+// caller order while the caller's arrays stream through, so the gather moves one record per
+// particle instead of four scattered 8-byte reads (FP32 solves read nothing else).
 __global__ void k_keys_periodic(int64_t n, const double *__restrict__ pos,
                                 const double *__restrict__ mass, SegInfo seg, KeyLayout kl,
                                 double box_x, double box_y, double box_z,
                                 uint64_t *__restrict__ key, int32_t *__restrict__ idx,
-                                DevState *ds)
+                                DevState *ds, uint4 *__restrict__ rec)
 {
     const int shift = kl.coord_bits - kl.lmax;
     const long long bx = __double_as_longlong(box_x), by = __double_as_longlong(box_y),
@@ -85,6 +88,7 @@ __global__ void k_keys_periodic(int64_t n, const double *__restrict__ pos,
         uint32_t Z = fix_periodic(z, seg.inv_q[2]);
         key[i] = morton3(X >> shift, Y >> shift, Z >> shift);
         idx[i] = (int32_t)i;
+        if (rec) rec[i] = make_uint4(X, Y, Z, __float_as_uint((float)m));
     }
     if (bad) atomicOr(&ds->sort_status, bad);
 }
@@ -105,7 +109,8 @@ __device__ __forceinline__ int group_of(const int64_t *__restrict__ offsets, int
 __global__ void k_keys_open(int64_t n, const double *__restrict__ pos,
                             const double *__restrict__ mass, const int64_t *__restrict__ offsets,
                             int64_t n_groups, const SegInfo *__restrict__ segs, KeyLayout kl,
-                            uint64_t *__restrict__ key, int32_t *__restrict__ idx, DevState *ds)
+                            uint64_t *__restrict__ key, int32_t *__restrict__ idx, DevState *ds,
+                            uint4 *__restrict__ rec)
 {
     const int shift = kl.coord_bits - kl.lmax;
     int bad = 0;
@@ -123,6 +128,7 @@ __global__ void k_keys_open(int64_t n, const double *__restrict__ pos,
         if (kl.seg_bits > 0) k |= (uint64_t)g << (3 * kl.lmax);
         key[i] = k;
         idx[i] = (int32_t)i;
+        if (rec) rec[i] = make_uint4(X, Y, Z, __float_as_uint((float)m));
     }
     if (bad) atomicOr(&ds->sort_status, bad);
 }
@@ -240,6 +246,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_radix_scatter(
         }
         __syncthreads();
     }
+}
+
+// FP32 sorts: the sorted fixed-point records are the caller-order records in sorted order.
+__global__ void k_gather_rec(int64_t n, const int32_t *__restrict__ idx, const uint4 *__restrict__ rec,
+                             uint4 *__restrict__ pfix)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        pfix[p] = rec[idx[p]];
 }
 
 __global__ void k_gather_periodic(int64_t n, const double *__restrict__ pos,
@@ -435,10 +450,10 @@ int blocks_for(int64_t n, int threads, int cap)
 int64_t radix_hist_size(int64_t n_max) { return (int64_t)kRadixBins * ((n_max + kTileKeys - 1) / kTileKeys + 1); }
 
 cudaError_t launch_keys_periodic(const SortArgs &a, int64_t n, const double *pos, const double *mass,
-                                 const SegInfo &seg, const double box[3], cudaStream_t st)
+                                 const SegInfo &seg, const double box[3], cudaStream_t st, uint4 *rec)
 {
     k_keys_periodic<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(
-        n, pos, mass, seg, a.kl, box[0], box[1], box[2], a.key[0], a.idx[0], a.ds);
+        n, pos, mass, seg, a.kl, box[0], box[1], box[2], a.key[0], a.idx[0], a.ds, rec);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }
@@ -459,11 +474,11 @@ cudaError_t launch_group_setup(const SortArgs &a, int64_t n_groups, const int64_
 }
 
 cudaError_t launch_keys_open(const SortArgs &a, int64_t n, const double *pos, const double *mass,
-                             const int64_t *offsets, int64_t n_groups, cudaStream_t st)
+                             const int64_t *offsets, int64_t n_groups, cudaStream_t st, uint4 *rec)
 {
     k_keys_open<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, pos, mass, offsets, n_groups,
                                                                   a.segs, a.kl, a.key[0], a.idx[0],
-                                                                  a.ds);
+                                                                  a.ds, rec);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }
@@ -507,6 +522,14 @@ cudaError_t launch_gather_open(const SortArgs &a, int64_t n, const double *pos, 
 {
     k_gather_open<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, pos, mass, idx, key, a.segs, a.kl,
                                                                    a.pfix, a.pdbl);
+    if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rec(const SortArgs &a, int64_t n, const int32_t *idx, const uint4 *rec,
+                              cudaStream_t st)
+{
+    k_gather_rec<<<blocks_for(n, 256, a.grid_cap), 256, 0, st>>>(n, idx, rec, a.pfix);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }
