@@ -308,7 +308,8 @@ __device__ __forceinline__ void flush(float4 *__restrict__ stage, const int *__r
         for (int ib = 0; ib < npair; ib += 32) {
             const int ie = ib + 32 < npair ? ib + 32 : npair;
             float2 pmw = f2(0.f, 0.f), pw = pmw, pdw = pmw, pc = pmw;
-#pragma unroll 4
+            // unrolled twice: measured faster than four times on the warm replay and the batch
+#pragma unroll 2
             for (int i = ib; i < ie; i++) {
                 const float4 A = st4[2 * (i << L.sh)], B = st4[2 * (i << L.sh) + 1];
                 const float2 dx = __fadd2_rn(f2(A.x, A.y), ntx);
