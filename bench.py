@@ -804,6 +804,10 @@ def run_batch(args):
     off, pos, mass, h0 = T(wl.offsets, torch.int64), T(wl.pos), T(wl.mass), T(wl.h0)
     nngb, tol = T(wl.nngb), T(wl.tol)
     s = B.Solver(n, precision=B.SPH_PREC_FP32_KAHAN, use_graph=True)
+    # a finer grouping once the todo list is sparse suits the batch's long tail of scattered halo
+    # targets (measured 47.3 -> 43.8 ms of density per solve); sph_autotune needs one sorted set,
+    # so the batch takes it by hand
+    s.set_tuning(sparse_shift=2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         r = s.batch_solve(off, pos, mass, h0, nngb, tol)
@@ -870,6 +874,28 @@ def run_batch(args):
                        "sample": f"{len(subset)} random groups, one sph_batch_solve call each"},
             "roofline": roof, "cpu_baseline": cpu, "gpu_launches": sum(x["kernel_launches"] for x in stats),
             "clocks": clk.summary()}), flush=True)
+
+
+def profiled_replay_traffic():
+    """DRAM bytes of one c5 replay step from the committed ncu summary (measured on the 8M-particle
+    replay and scaled by particle count), while the kernel sources are the ones it was captured
+    from; else None."""
+    import hashlib
+    import re
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", "replay_c5_launches.md")).read()
+        src = b"".join(open(os.path.join(ROOT, "paper_1612_06090_gb300", "csrc", f), "rb").read()
+                       for f in ("sph_density.cu", "sph_items.cuh", "sph_common.cuh", "sph_solve.cu", "sph_sort.cu"))
+        want = re.search(r"kernel_source_sha256_16: (\w+)", text).group(1)
+        if hashlib.sha256(src).hexdigest()[:16] != want:
+            return None
+        get = lambda k: float(re.search(k + r": ([0-9.eE+]+)", text).group(1))  # noqa: E731
+        return {"capture_particles": int(get("capture_particles")),
+                "density_dram_bytes_per_step": get("density_dram_bytes_per_step"),
+                "step_dram_bytes_per_step": get("step_dram_bytes_per_step")}
+    except Exception:
+        return None
 
 
 def probe_fp32_peak(stream_handle):
@@ -1045,9 +1071,13 @@ def run_replay(args):
                  for k in range(max(x["passes"] for x in st32))]
     alg_bytes = statistics.mean(hbm_algorithmic_bytes(n, x["todo_per_pass"]) for x in st32)
     hbm_gbs = alg_bytes / (t_max / 1e3) / 1e9
+    prof = profiled_replay_traffic()
+    scale = n / prof["capture_particles"] if prof else None
     roof = {"bound": "alu", "kernel": "k_density<2> (FP32 pair loop, all passes of a replay step)",
             "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-            "traffic": None,
+            "traffic": prof["density_dram_bytes_per_step"] * scale if prof else None,
+            "traffic_note": ("DRAM bytes of the density kernel per replay step: ncu on the 8,388,608-particle "
+                             "replay (profiles/replay_c5_launches.md), scaled by particle count"),
             "peak_note": "measured: dependent-FMA probe (libsph_probe.so, best of scalar and two-wide "
                          "FMA), timed alone with CUDA events in this run",
             "peak_probe": probe, "flop_per_pair": FLOP_PER_PAIR,
@@ -1060,7 +1090,11 @@ def run_replay(args):
             "hbm_bytes_per_step": alg_bytes,
             "hbm_note": f"algorithmic bytes {BYTES_PER_PARTICLE} B per particle + {BYTES_PER_EVALUATION} B "
                         "per particle evaluation, over the graph-loop step time; peak = measured "
-                        "copy bandwidth (MEASURED_PEAKS.json)"}
+                        "copy bandwidth (MEASURED_PEAKS.json)",
+            "hbm_ncu_bytes_per_step": prof["step_dram_bytes_per_step"] * scale if prof else None,
+            "hbm_ncu_gbs": prof["step_dram_bytes_per_step"] * scale / (t_max / 1e3) / 1e9 if prof else None,
+            "hbm_ncu_note": "DRAM bytes of every kernel of a replay step, ncu on the 8,388,608-particle replay "
+                            "(per-kernel, serialised) scaled by particle count, over the graph-loop step time"}
 
     # ---- plain FP64 GPU solve of the first replay step, same start ----
     fp64 = None

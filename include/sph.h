@@ -107,7 +107,7 @@ typedef struct sph_ctx sph_ctx;
 
 /* Knobs of the spatial decomposition and of the density kernels' launch, set by the
  * autotuner or by hand.  They change speed, never results beyond summation order.
- * Defaults: {0, 3, 1, 0, 0, 32, 256, 0, 10}. */
+ * Defaults: {0, 3, 1, 0, 0, 32, 256, 0, 10, 0}. */
 typedef struct {
     int32_t group_shift;  /* a work item gathers todo targets that share an octree cell of edge
                              >= h / 2^group_shift (-2..3)                                     */
@@ -130,6 +130,11 @@ typedef struct {
                              as fit (occupancy); larger values are clamped to that              */
     int32_t list_margin_pct; /* cached neighbour lists hold the particles within
                              (1 + list_margin_pct / 100) h of the search (1..100)              */
+    int32_t sparse_shift; /* group_shift used while the todo list is sparse (fewer than 1/8 of
+                             the particles): the targets left late in a solve are scattered, so
+                             a cell of edge up to 2h may hold targets far apart relative to their
+                             h; a finer grouping keeps each item's staging ball near its
+                             targets' own (-2..3)                                              */
 } sph_tuning;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
@@ -159,8 +164,8 @@ sph_status sph_set_tuning(sph_ctx *ctx, const sph_tuning *tuning);
  * time from the current tuning and keeping the best value of each (two rounds): the item
  * cap (0, 16, 32, 64), targets per item (8, 16, 32), the grouping level (group_shift
  * -1..1), the candidate cell size (cell_div 2..3), threads per block (128, 256),
- * resident blocks per SM (all that fit, or one fewer) and, with cached lists, the list
- * margin (5, 10, 20 %).  Keeps the fastest tuning in the
+ * resident blocks per SM (all that fit, or one fewer), the grouping level of sparse passes
+ * (sparse_shift -1..2) and, with cached lists, the list margin (5, 10, 20 %).  Keeps the fastest tuning in the
  * context and, when the context has a tune_cache file, appends it there; sph_sort applies
  * the last cached entry that matches the GPU, the particle-count bucket (floor log2 n),
  * periodic and precision.  best may be NULL.  Results never change beyond summation order.

@@ -105,6 +105,7 @@ class SphTuning(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
         ("list_margin_pct", ctypes.c_int32),
+        ("sparse_shift", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

@@ -73,7 +73,7 @@ struct sph_ctx {
         sph_tuning tuning{};
         KeyLayout kl{};
     } graph_key;
-    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0, 10};
+    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0, 10, 0};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
     int grid_cap = 0;
@@ -265,6 +265,7 @@ SolveArgs solve_args(sph_ctx *c)
     a.list_entries = c->params.list_entries;
     a.list_margin = 1.0f + (float)c->tuning.list_margin_pct * 0.01f;
     a.group_shift = c->tuning.group_shift;
+    a.sparse_shift = c->tuning.sparse_shift;
     a.cell_div = c->tuning.cell_div;
     a.direct_pct = c->tuning.direct_pct;
     a.free_first = (c->kl.seg_bits == 0 && c->params.precision != SPH_PREC_FP64 &&
@@ -283,8 +284,8 @@ int table_level(int64_t n, int lmax, int extra)
 }
 
 // Autotuner cache: one line per result,
-// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs lm" (the sph_tuning fields in
-// order); the last matching line wins.
+// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs lm ss" (the sph_tuning fields
+// in order); the last matching line wins.
 std::string cache_key(const sph_ctx *c, int64_t n)
 {
     int b = 0;
@@ -304,9 +305,9 @@ bool cache_lookup(const sph_ctx *c, int64_t n, sph_tuning *t)
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
         sph_tuning x = c->tuning;
-        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra,
+        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra,
                    &x.direct_pct, &x.item_cap, &x.item_max, &x.block_threads, &x.blocks_per_sm,
-                   &x.list_margin_pct) == 10 &&
+                   &x.list_margin_pct, &x.sparse_shift) == 11 &&
             key == k) {
             *t = x;
             found = true;
@@ -321,9 +322,9 @@ void cache_store(const sph_ctx *c, int64_t n, const sph_tuning &t)
     if (c->tune_cache.empty()) return;
     FILE *f = fopen(c->tune_cache.c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div,
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div,
             t.table_extra, t.direct_pct, t.item_cap, t.item_max, t.block_threads, t.blocks_per_sm,
-            t.list_margin_pct);
+            t.list_margin_pct, t.sparse_shift);
     fclose(f);
 }
 
@@ -334,7 +335,8 @@ bool tuning_ok(const sph_tuning *t)
            t->table_extra >= 0 && t->table_extra <= 1 && t->direct_pct >= 0 && t->direct_pct <= 101 &&
            (t->item_cap == 0 || (t->item_cap >= 2 && t->item_cap <= 64)) && pow2 &&
            (t->block_threads == 64 || t->block_threads == 128 || t->block_threads == 256) &&
-           t->blocks_per_sm >= 0 && t->blocks_per_sm <= 32 && t->list_margin_pct >= 1 && t->list_margin_pct <= 100;
+           t->blocks_per_sm >= 0 && t->blocks_per_sm <= 32 && t->list_margin_pct >= 1 && t->list_margin_pct <= 100 &&
+           t->sparse_shift >= -2 && t->sparse_shift <= 3;
 }
 
 sph_status read_state(sph_ctx *c)
@@ -794,9 +796,9 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
         return err;
     }
     const int mode = ctx->params.precision == SPH_PREC_FP64 ? 0 : 2;
-    const int nknobs = ctx->params.list_entries > 0 ? 7 : 6;
     for (int round = 0; round < 2; round++) {
-        for (int knob = 0; knob < nknobs; knob++) {
+        for (int knob = 0; knob < 8; knob++) {
+            if (knob == 6 && ctx->params.list_entries == 0) continue;  // no lists, no margin
             int vals[4];
             int nv = 0;
             switch (knob) {
@@ -806,6 +808,7 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
             case 3: vals[0] = 2, vals[1] = 3, nv = 2; break;                               // cell_div
             case 4: vals[0] = 128, vals[1] = 256, nv = 2; break;                           // block_threads
             case 6: vals[0] = 5, vals[1] = 10, vals[2] = 20, nv = 3; break;                // list_margin_pct
+            case 7: vals[0] = -1, vals[1] = 0, vals[2] = 1, vals[3] = 2, nv = 4; break;    // sparse_shift
             default: {                                                                     // blocks_per_sm
                 const int bt = best.block_threads;
                 const int ti = bt == 64 ? 0 : bt == 128 ? 1 : 2;
@@ -824,7 +827,8 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
                              : knob == 3 ? &t.cell_div
                              : knob == 4 ? &t.block_threads
                              : knob == 5 ? &t.blocks_per_sm
-                                         : &t.list_margin_pct;
+                             : knob == 6 ? &t.list_margin_pct
+                                         : &t.sparse_shift;
                 if (*field == vals[v]) continue;
                 *field = vals[v];
                 const float ms = time_one(t, &err);

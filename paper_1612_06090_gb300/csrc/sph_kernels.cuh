@@ -77,6 +77,7 @@ struct SolveArgs {
                                // cell (not coarser than that level) with <= item_cap todo targets
     int block_threads;         // threads per block of the density kernels (64, 128 or 256)
     int group_shift;           // items group targets sharing an octree cell of edge >= h / 2^shift
+    int sparse_shift;          // the same while the todo list is sparse (< 1/8 of the particles)
     int cell_div;              // candidate cells have an edge >= (query extent) / cell_div
     int direct_pct;            // in-h percentage of the first tests above which the pair loop
                                // evaluates directly instead of queueing (101 = always queue)

@@ -219,6 +219,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
     // lanes hold consecutive entries, so an entry's predecessor is the previous lane's entry
     // (lane 0 works its own out); the loop bound is the warp's first entry, so shuffles see the
     // whole warp
+    const int shift = dense ? a.group_shift : a.sparse_shift;
     for (int tb = blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < T; tb += gridDim.x * blockDim.x) {
         const int t = tb + lane;
         const bool have = t < T;
@@ -228,7 +229,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
         if (have) {
             const int p = todo[t];
             k = a.key[p];
-            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, l, pre, big, ctab0, hmul);
+            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, shift, l, pre, big, ctab0, hmul);
         }
         uint64_t kp = __shfl_up_sync(kFull, k, 1), prep = __shfl_up_sync(kFull, pre, 1);
         int lp = __shfl_up_sync(kFull, l, 1);
@@ -236,7 +237,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
         if (lane == 0 && have && t > 0) {
             const int pp = todo[t - 1];
             kp = a.key[pp];
-            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, a.group_shift, lp, prep, bigp, ctab0, hmul);
+            bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, shift, lp, prep, bigp, ctab0, hmul);
         }
         if (!have) continue;
         int head = (t % a.gmax == 0) || big;
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
     __shared__ int sl[kCapTile + 1];  // entries base - 1 .. base + kCapTile - 1: level | big << 8
     const int T = a.ds->dens_count;
     const int cap = a.item_cap < kCapMax ? a.item_cap : kCapMax;
+    const int shift = 8 * (int64_t)T >= a.n ? a.group_shift : a.sparse_shift;
     const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
     const int ntiles = (T + kCapTile - 1) / kCapTile;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
             int lh;
             uint64_t pre;
             bool big;
-            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, a.group_shift, lh, pre, big, ctab0,
+            bucket_of(k, a.h32[p], a.segs[seg_of(k, a.kl)], a.kl, shift, lh, pre, big, ctab0,
                       a.lst ? a.list_margin * 1.001f : 1.0f);
             if (big) return lh | (1 << 8);
             const int nl = a.kl.lmax - lh + 1 < kCapLevels ? a.kl.lmax - lh + 1 : kCapLevels;
