@@ -54,7 +54,6 @@ KNN_METRIC = "kNN SPH particles/s (h = K-th neighbour distance, rho at h)"
 # one neighbour-list entry: a squared distance from three offsets (3 subtractions, 3 multiplies,
 # 2 additions); the radius compare and the selection are not counted
 FLOP_PER_LIST_ENTRY = 8
-FP32_LANES_PER_SM = 128
 
 
 def parse():
@@ -479,14 +478,14 @@ def run_native(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    peak_tflops, probe = probe_fp32_peak(stream.cuda_stream)
     achieved = pairs * FLOP_PER_PAIR / (dens_ms / 1e3) / 1e12 if dens_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_density<2> (FP32 pair loop)", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
             "traffic": profiled_traffic() if args.config == "c2" and not args.n and args.kernel == "m4" else None,
             "traffic_note": "mean DRAM bytes per density pass (ncu, profiles/density_fp32_c2_1M.md)",
-            "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
+            "peak_note": "measured: dependent-FMA probe (libsph_probe.so), timed alone with CUDA events",
+            "peak_probe": probe,
             "flop_per_pair": FLOP_PER_PAIR, "pairs_per_step": pairs // max(1, len(st32)),
             "density_ms_per_step": dens_ms / max(1, len(st32)),
             "density_launches_per_step": dens_launch / max(1, len(st32)),
@@ -660,15 +659,15 @@ def run_knn(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    peak_tflops, probe = probe_fp32_peak(stream.cuda_stream)
     knn_ms = sum(s_["density_ms"] for s_ in st32)
     listed = sum(s_["pair_evals"] for s_ in st32)
     achieved = listed * FLOP_PER_LIST_ENTRY / (knn_ms / 1e3) / 1e12 if knn_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_knn<FP32> (neighbour lists + warp radix select)",
             "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
             "traffic": None,
-            "peak_note": f"FP32 FMA peak {sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz",
+            "peak_note": "measured: dependent-FMA probe (libsph_probe.so), timed alone with CUDA events",
+            "peak_probe": probe,
             "flop_per_list_entry": FLOP_PER_LIST_ENTRY,
             "list_entries_per_step": listed // max(1, len(st32)),
             "candidates_streamed_per_step": sum(s_["pair_tests"] for s_ in st32) // max(1, len(st32)),
@@ -772,10 +771,10 @@ def profiled_traffic():
         return None
 
 
-def roofline_from(stats_list, sms, sm_max_mhz, kernel):
+def roofline_from(stats_list, peak, kernel):
+    """Density-stage roofline from solve statistics against the measured FP32 FMA rate."""
     dens_ms = sum(s["density_ms"] for s in stats_list)
     pairs = sum(s["pair_evals"] for s in stats_list)
-    peak = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     ach = pairs * FLOP_PER_PAIR / (dens_ms / 1e3) / 1e12 if dens_ms > 0 else 0.0
     return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": None, "flop_per_pair": FLOP_PER_PAIR,
@@ -832,6 +831,7 @@ def run_batch(args):
     subset = np.sort(rng.choice(G, size=min(G, 300), replace=False))
     loop_particles, loop_time = 0, 0.0
     one = B.Solver(int(np.diff(wl.offsets).max()), precision=B.SPH_PREC_FP32_KAHAN, use_graph=False)
+    one.set_tuning(sparse_shift=2)
     for gi in subset:
         a, e = int(wl.offsets[gi]), int(wl.offsets[gi + 1])
         args_g = (T([0, e - a], torch.int64), T(wl.pos[:, a:e]), T(wl.mass[a:e]), T(wl.h0[a:e]),
@@ -844,9 +844,10 @@ def run_batch(args):
         loop_particles += e - a
     # density roofline from one host-driven batched solve (per-pass kernel events)
     s2 = B.Solver(n, precision=B.SPH_PREC_FP32_KAHAN, use_graph=False)
+    s2.set_tuning(sparse_shift=2)
     r2 = s2.batch_solve(off, pos, mass, h0, nngb, tol)
-    props = torch.cuda.get_device_properties(dev)
-    roof = roofline_from([r2["stats"]], props.multi_processor_count, 2070.0, "k_density<2> (FP32 pair loop)")
+    fp32_peak, _ = probe_fp32_peak(torch.cuda.current_stream().cuda_stream)
+    roof = roofline_from([r2["stats"]], fp32_peak, "k_density<2> (FP32 pair loop)")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
