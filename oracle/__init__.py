@@ -16,6 +16,8 @@ h_update(...)                one step of that iteration's h update
 batch_solve(...)             the same over independent non-periodic groups
 knn(...)                     h = distance to the K-th nearest particle, rho at that h
                              (Sec. IV-D, the selection of the K nearest)
+interact(...)                velocity mean, dispersion, divergence and curl over the same
+                             neighbour sets (the further pair computations of Listing 1)
 """
 from __future__ import annotations
 
@@ -100,6 +102,10 @@ def _load():
     lib.oracle_knn.restype = ctypes.c_int
     lib.oracle_knn.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int64, ip, ctypes.c_int, dp, dp, dp, ip, i32p, ctypes.c_int]
+    lib.oracle_interact.restype = ctypes.c_int
+    lib.oracle_interact.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int,
+                                    ctypes.c_int64, ip, dp, ctypes.c_int, dp, dp, dp, dp, dp, ip, dp,
+                                    ctypes.c_int]
     lib.oracle_h_update.restype = ctypes.c_double
     lib.oracle_h_update.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     dp, dp]
@@ -283,3 +289,40 @@ def knn(pos, mass, k, box=(1.0, 1.0, 1.0), periodic=True, targets=None, mode="gr
     if rc != 0:
         raise MemoryError("oracle_knn failed to allocate")
     return {"h": h, "rho": rho, "nw": nw, "count": count, "status": status}
+
+
+def interact(pos, mass, vel, h, box=(1.0, 1.0, 1.0), periodic=True, targets=None, mode="grid",
+             kernel="m4"):
+    """Velocity-field estimates over each target's neighbours at its h (gather form).
+
+    pos, vel: (3, N); mass: (N,); h: one value per target (targets=None: all N particles).
+    Returns rho (Eq. 1), vmean (3, T) = (1/rho) sum m W v_j, sigma2 = (1/rho) sum m W
+    |v_j - vmean|^2, div = (1/rho) sum m (v_j - v_i) . grad_i W, curl (3, T) = (1/rho) sum
+    m (v_i - v_j) x grad_i W, count (#{r < h}, self included) and the error scales vscale2
+    ((1/rho) sum m W |v_j - v_i|^2), gabs ((1/rho) sum m |grad W| |v_j - v_i|), gnorm ((1/rho)
+    sum m |grad W|) and vmax (largest velocity component magnitude among the neighbours).
+    """
+    lib = _load()
+    pos = _f64(pos)
+    vel = _f64(vel)
+    mass = _f64(mass)
+    n = mass.shape[0]
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else tg.shape[0]
+    h = _f64(np.broadcast_to(np.asarray(h, dtype=np.float64), (nt,)))
+    box = _f64(box)
+    rho, sigma2, div = np.empty(nt), np.empty(nt), np.empty(nt)
+    vmean, curl = np.empty((3, nt)), np.empty((3, nt))
+    count = np.empty(nt, dtype=np.int64)
+    scales = np.empty((4, nt))
+    x, y, z = (np.ascontiguousarray(pos[d]) for d in range(3))
+    vx, vy, vz = (np.ascontiguousarray(vel[d]) for d in range(3))
+    rc = lib.oracle_interact(n, _dp(x), _dp(y), _dp(z), _dp(mass), _dp(vx), _dp(vy), _dp(vz), _dp(box),
+                             int(bool(periodic)), nt if tg is not None else -1,
+                             _ip(tg) if tg is not None else None, _dp(h), _MODES[mode], _dp(rho),
+                             _dp(vmean), _dp(sigma2), _dp(div), _dp(curl), _ip(count), _dp(scales),
+                             KERNELS[kernel])
+    if rc != 0:
+        raise MemoryError("oracle_interact failed to allocate")
+    return {"rho": rho, "vmean": vmean, "sigma2": sigma2, "div": div, "curl": curl, "count": count,
+            "vscale2": scales[0], "gabs": scales[1], "gnorm": scales[2], "vmax": scales[3]}

@@ -37,6 +37,9 @@
  *    and counts of that evaluation.
  *  - The k-nearest-neighbour form of h (Sec. IV-D): h_i = distance to the K-th nearest
  *    particle, rho_i by Eq. (1) at that h (oracle_knn).
+ *  - Further pair computations over the same neighbour sets (the "other particle
+ *    interactions" of Listing 1): kernel-weighted mean velocity, velocity dispersion,
+ *    velocity divergence and curl at the converged h (oracle_interact).
  *
  * Neighbour search: a stack of uniform FP64 bucket grids (cell size box / 2^k).  For a
  * target with smoothing length h the grid with the coarsest cells no larger than h is
@@ -278,15 +281,12 @@ static void eval_brute(const pset *ps, int64_t i, double h, double near_rel, acc
     for (int64_t j = 0; j < ps->n; j++) pair(ps, i, j, h, h2, near_rel, a);
 }
 
-/* Scan every bucket meeting [x_i - h, x_i + h] in each dimension. */
-static void eval_grid(const pset *ps, const bucket_grid *bg, int64_t i, double h,
-                      double near_rel, acc_t *a)
+/* First bucket and bucket count per dimension of the buckets meeting [x_i - h, x_i + h]
+ * (a periodic row that the interval covers entirely is taken once, from bucket 0). */
+static void bucket_box(const pset *ps, const bucket_grid *bg, const double xi[3], double h,
+                       int64_t lo[3], int64_t cnt[3])
 {
-    double h2 = h * h;
-    const double xi[3] = {ps->x[i], ps->y[i], ps->z[i]};
-    int64_t lo[3], cnt[3];
     int64_t g = bg->g;
-    memset(a, 0, sizeof(*a));
     for (int d = 0; d < 3; d++) {
         double c = bg->cell[d];
         int64_t a0 = (int64_t)floor((xi[d] - h - ps->origin[d]) / c);
@@ -306,6 +306,18 @@ static void eval_grid(const pset *ps, const bucket_grid *bg, int64_t i, double h
             cnt[d] = a1 >= a0 ? a1 - a0 + 1 : 0;
         }
     }
+}
+
+/* Scan every bucket meeting [x_i - h, x_i + h] in each dimension. */
+static void eval_grid(const pset *ps, const bucket_grid *bg, int64_t i, double h,
+                      double near_rel, acc_t *a)
+{
+    double h2 = h * h;
+    const double xi[3] = {ps->x[i], ps->y[i], ps->z[i]};
+    int64_t lo[3], cnt[3];
+    int64_t g = bg->g;
+    memset(a, 0, sizeof(*a));
+    bucket_box(ps, bg, xi, h, lo, cnt);
     for (int64_t kz = 0; kz < cnt[2]; kz++) {
         int64_t cz = lo[2] + kz;
         if (ps->periodic) cz = ((cz % g) + g) % g;
@@ -682,6 +694,214 @@ int oracle_knn(int64_t n, const double *x, const double *y, const double *z, con
     for (int lv = 0; lv <= ORACLE_MAX_LEVEL; lv++)
         if (grids[lv].built) free_grid(&grids[lv]);
     return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Other particle interactions (the second phase of Listing 1)                           */
+/* ------------------------------------------------------------------------------------ */
+
+/* The paper's density loop leaves a place for further pair computations over the same
+ * neighbours ("other particle interaction computations"; Sec. II-A calls this the second
+ * phase of the particle interactions) without fixing them.  The ones taken here are the
+ * standard SPH velocity-field estimates over the neighbour set of Eq. (1), gather form,
+ * at the target's converged h:
+ *   rho_i         = sum_j m_j W_ij                                   (Eq. 1)
+ *   vbar_i        = (1 / rho_i) sum_j m_j W_ij v_j                   kernel-weighted mean
+ *   sigma2_i      = (1 / rho_i) sum_j m_j W_ij |v_j - vbar_i|^2      velocity dispersion
+ *   (div v)_i     = (1 / rho_i) sum_j m_j (v_j - v_i) . grad_i W_ij
+ *   (curl v)_i    = (1 / rho_i) sum_j m_j (v_i - v_j) x grad_i W_ij
+ * with W_ij = W(r_ij, h_i) and grad_i W_ij = dW/dr (r_ij) (r_i - r_j) / r_ij, zero at
+ * r_ij = 0 (the kernel is flat there); dW/dr = sigma h^-4 w'(q) and w'(q) = -mqdw(q) / q.
+ * The neighbours are j with r_ij < h_i, the self pair included, r_i - r_j the minimum image
+ * when periodic, all formed as in pair().  The mean is taken first and the dispersion
+ * about it in a second sweep over the list, as the definition reads.
+ * Scales reported beside the values (for error bounds): vscale2 = (1 / rho_i) sum_j m_j W_ij
+ * |v_j - v_i|^2, gabs = (1 / rho_i) sum_j m_j |grad_i W_ij| |v_j - v_i|, gnorm = (1 / rho_i)
+ * sum_j m_j |grad_i W_ij|, vmax = max over the neighbours of max_d |v_j,d|. */
+typedef struct {
+    int64_t j;
+    double d[3]; /* r_i - r_j */
+    double r;
+} nbr_t;
+
+typedef struct {
+    nbr_t *e;
+    int64_t n, cap;
+} nbr_list;
+
+static int nbr_push(nbr_list *L, int64_t j, const double d[3], double r)
+{
+    if (L->n == L->cap) {
+        int64_t cap = L->cap ? 2 * L->cap : 256;
+        nbr_t *e = (nbr_t *)realloc(L->e, (size_t)cap * sizeof(nbr_t));
+        if (!e) return -1;
+        L->e = e;
+        L->cap = cap;
+    }
+    L->e[L->n].j = j;
+    for (int k = 0; k < 3; k++) L->e[L->n].d[k] = d[k];
+    L->e[L->n].r = r;
+    L->n++;
+    return 0;
+}
+
+/* Append j to the list when r_ij < h (the neighbour test of pair()). */
+static int nbr_test(const pset *ps, int64_t i, int64_t j, double h2, nbr_list *L)
+{
+    const double *c[3] = {ps->x, ps->y, ps->z};
+    double s[3]; /* r_j - r_i */
+    for (int k = 0; k < 3; k++) {
+        s[k] = c[k][j] - c[k][i];
+        if (ps->periodic) s[k] = min_image(s[k], ps->box[k]);
+    }
+    double r2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+    if (r2 < h2) {
+        const double d[3] = {-s[0], -s[1], -s[2]};
+        return nbr_push(L, j, d, sqrt(r2));
+    }
+    return 0;
+}
+
+static int collect(const pset *ps, const bucket_grid *bg, int64_t i, double h, nbr_list *L)
+{
+    double h2 = h * h;
+    L->n = 0;
+    if (!bg) {
+        for (int64_t j = 0; j < ps->n; j++)
+            if (nbr_test(ps, i, j, h2, L)) return -1;
+        return 0;
+    }
+    const double xi[3] = {ps->x[i], ps->y[i], ps->z[i]};
+    int64_t lo[3], cnt[3];
+    int64_t g = bg->g;
+    bucket_box(ps, bg, xi, h, lo, cnt);
+    for (int64_t kz = 0; kz < cnt[2]; kz++) {
+        int64_t cz = lo[2] + kz;
+        if (ps->periodic) cz = ((cz % g) + g) % g;
+        for (int64_t ky = 0; ky < cnt[1]; ky++) {
+            int64_t cy = lo[1] + ky;
+            if (ps->periodic) cy = ((cy % g) + g) % g;
+            for (int64_t kx = 0; kx < cnt[0]; kx++) {
+                int64_t cx = lo[0] + kx;
+                if (ps->periodic) cx = ((cx % g) + g) % g;
+                int64_t id = cx + g * (cy + g * cz);
+                int64_t s = lower_bound_id(bg->ids, ps->n, id);
+                for (int64_t p = s; p < ps->n && bg->ids[p] == id; p++)
+                    if (nbr_test(ps, i, bg->order[p], h2, L)) return -1;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Velocity-field estimates of every target at its h (definitions above).  vel: three
+ * arrays vx, vy, vz over all particles.  Outputs indexed by target position; vmean and
+ * curl are three arrays of n_targets each (x block, y block, z block); scales holds
+ * vscale2, gabs, gnorm, vmax in four blocks.  mode 0 = bucket grids, 1 = brute force. */
+int oracle_interact(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                    const double *vx, const double *vy, const double *vz, const double *box,
+                    int periodic, int64_t n_targets, const int64_t *targets, const double *h,
+                    int mode, double *rho, double *vmean, double *sigma2, double *divv,
+                    double *curlv, int64_t *count, double *scales, int kernel)
+{
+    const double pi = 3.14159265358979323846;
+    pset ps;
+    setup_pset(&ps, n, x, y, z, m, box, periodic, kernel);
+    if (n_targets < 0) n_targets = n;
+    const double sigma = kernel ? 1365.0 / (64.0 * pi) : 8.0 / pi;
+    const double *v[3] = {vx, vy, vz};
+    bucket_grid grids[ORACLE_MAX_LEVEL + 1];
+    memset(grids, 0, sizeof(grids));
+    if (mode == 0) {
+        for (int64_t t = 0; t < n_targets; t++) {
+            int k = level_for(&ps, h[t]);
+            if (!grids[k].built && build_grid(&ps, k, &grids[k]) != 0) return -1;
+        }
+    }
+    int failed = 0;
+    #pragma omp parallel
+    {
+        nbr_list L = {NULL, 0, 0};
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t t = 0; t < n_targets; t++) {
+            const int64_t i = targets ? targets[t] : t;
+            const double hi = h[t];
+            if (collect(&ps, mode == 0 ? &grids[level_for(&ps, hi)] : NULL, i, hi, &L)) {
+                #pragma omp atomic write
+                failed = 1;
+                continue;
+            }
+            /* density, Eq. (1) */
+            double r_sum = 0.0;
+            for (int64_t k = 0; k < L.n; k++) {
+                double q = L.e[k].r / hi;
+                double w = kernel ? oracle_w_c6(q) : oracle_w(q);
+                double W = sigma / (hi * hi * hi) * w;
+                r_sum += ps.m[L.e[k].j] * W;
+            }
+            const double rh = r_sum;
+            /* kernel-weighted mean velocity */
+            double vb[3] = {0.0, 0.0, 0.0};
+            for (int64_t k = 0; k < L.n; k++) {
+                const int64_t j = L.e[k].j;
+                double q = L.e[k].r / hi;
+                double w = kernel ? oracle_w_c6(q) : oracle_w(q);
+                double W = sigma / (hi * hi * hi) * w;
+                for (int d = 0; d < 3; d++) vb[d] += ps.m[j] * W * v[d][j];
+            }
+            for (int d = 0; d < 3; d++) vb[d] = vb[d] / rh;
+            /* dispersion about the mean; divergence and curl; the scales */
+            double s2 = 0.0, dv_sum = 0.0, cv[3] = {0.0, 0.0, 0.0};
+            double vs2 = 0.0, gabs = 0.0, gnorm = 0.0, vmax = 0.0;
+            for (int64_t k = 0; k < L.n; k++) {
+                const int64_t j = L.e[k].j;
+                const double r = L.e[k].r;
+                double q = r / hi;
+                double w = kernel ? oracle_w_c6(q) : oracle_w(q);
+                double W = sigma / (hi * hi * hi) * w;
+                double e[3], dvel[3];
+                for (int d = 0; d < 3; d++) {
+                    e[d] = v[d][j] - vb[d];
+                    dvel[d] = v[d][j] - v[d][i];
+                    if (fabs(v[d][j]) > vmax) vmax = fabs(v[d][j]);
+                }
+                s2 += ps.m[j] * W * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+                vs2 += ps.m[j] * W * (dvel[0] * dvel[0] + dvel[1] * dvel[1] + dvel[2] * dvel[2]);
+                /* grad_i W_ij = dW/dr (r_i - r_j) / r, zero at r = 0 */
+                double gW[3] = {0.0, 0.0, 0.0};
+                if (r > 0.0) {
+                    double wp = -(kernel ? oracle_mqdw_c6(q) : oracle_mqdw(q)) / q;
+                    double dWdr = sigma / (hi * hi * hi * hi) * wp;
+                    for (int d = 0; d < 3; d++) gW[d] = dWdr * (L.e[k].d[d] / r);
+                }
+                dv_sum += ps.m[j] * (dvel[0] * gW[0] + dvel[1] * gW[1] + dvel[2] * gW[2]);
+                /* (v_i - v_j) x grad_i W */
+                const double u[3] = {-dvel[0], -dvel[1], -dvel[2]};
+                cv[0] += ps.m[j] * (u[1] * gW[2] - u[2] * gW[1]);
+                cv[1] += ps.m[j] * (u[2] * gW[0] - u[0] * gW[2]);
+                cv[2] += ps.m[j] * (u[0] * gW[1] - u[1] * gW[0]);
+                double gn = sqrt(gW[0] * gW[0] + gW[1] * gW[1] + gW[2] * gW[2]);
+                gnorm += ps.m[j] * gn;
+                gabs += ps.m[j] * gn * sqrt(dvel[0] * dvel[0] + dvel[1] * dvel[1] + dvel[2] * dvel[2]);
+            }
+            rho[t] = rh;
+            for (int d = 0; d < 3; d++) {
+                vmean[d * n_targets + t] = vb[d];
+                curlv[d * n_targets + t] = cv[d] / rh;
+            }
+            sigma2[t] = s2 / rh;
+            divv[t] = dv_sum / rh;
+            count[t] = L.n;
+            scales[t] = vs2 / rh;
+            scales[n_targets + t] = gabs / rh;
+            scales[2 * n_targets + t] = gnorm / rh;
+            scales[3 * n_targets + t] = vmax;
+        }
+        free(L.e);
+    }
+    for (int k = 0; k <= ORACLE_MAX_LEVEL; k++)
+        if (grids[k].built) free_grid(&grids[k]);
+    return failed ? -1 : 0;
 }
 
 int oracle_num_threads(void)

@@ -22,6 +22,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
+IP = "test_oracle_interact_pins.py::"  # pins in that file; the rest are in test_oracle_pins.py
+
 # (what the mistake is, the original text, the planted text, the pin that must fail)
 MUTANTS = [
     ("w: cubic coefficient",
@@ -216,6 +218,50 @@ MUTANTS = [
      "if (gs.passes > st->passes) st->passes = gs.passes;",
      "st->passes += gs.passes;",
      "test_batch_equals_groups_solved_alone"),
+    ("interact: gradient sign",
+     "double wp = -(kernel ? oracle_mqdw_c6(q) : oracle_mqdw(q)) / q;",
+     "double wp = (kernel ? oracle_mqdw_c6(q) : oracle_mqdw(q)) / q;",
+     IP + "test_two_particles_closed_form"),
+    ("interact: gradient h^-3",
+     "double dWdr = sigma / (hi * hi * hi * hi) * wp;",
+     "double dWdr = sigma / (hi * hi * hi) * wp;",
+     IP + "test_linear_field_on_a_lattice"),
+    ("interact: gradient not a unit vector",
+     "gW[d] = dWdr * (L.e[k].d[d] / r);",
+     "gW[d] = dWdr * L.e[k].d[d];",
+     IP + "test_two_particles_closed_form"),
+    ("interact: curl operands swapped",
+     "const double u[3] = {-dvel[0], -dvel[1], -dvel[2]};",
+     "const double u[3] = {dvel[0], dvel[1], dvel[2]};",
+     IP + "test_linear_field_on_a_lattice"),
+    ("interact: curl y component",
+     "cv[1] += ps.m[j] * (u[2] * gW[0] - u[0] * gW[2]);",
+     "cv[1] += ps.m[j] * (u[0] * gW[2] - u[2] * gW[0]);",
+     IP + "test_two_particles_closed_form"),
+    ("interact: dispersion about v_i",
+     "e[d] = v[d][j] - vb[d];",
+     "e[d] = v[d][j] - v[d][i];",
+     IP + "test_two_particles_closed_form"),
+    ("interact: mean not normalised",
+     "for (int d = 0; d < 3; d++) vb[d] = vb[d] / rh;",
+     "for (int d = 0; d < 3; d++) vb[d] = vb[d] / (rh * hi);",
+     IP + "test_uniform_field_and_galilean_boost"),
+    ("interact: divergence of v_i - v_j",
+     "dv_sum += ps.m[j] * (dvel[0] * gW[0] + dvel[1] * gW[1] + dvel[2] * gW[2]);",
+     "dv_sum -= ps.m[j] * (dvel[0] * gW[0] + dvel[1] * gW[1] + dvel[2] * gW[2]);",
+     IP + "test_linear_field_on_a_lattice"),
+    ("interact: target mass",
+     "r_sum += ps.m[L.e[k].j] * W;",
+     "r_sum += ps.m[i] * W;",
+     IP + "test_matches_numpy_brute_force"),
+    ("interact: self pair dropped",
+     "    if (r2 < h2) {\n        const double d[3] = {-s[0], -s[1], -s[2]};",
+     "    if (r2 < h2 && i != j) {\n        const double d[3] = {-s[0], -s[1], -s[2]};",
+     IP + "test_matches_numpy_brute_force"),
+    ("interact: z image uses y box",
+     "s[k] = min_image(s[k], ps->box[k]);",
+     "s[k] = min_image(s[k], ps->box[k > 1 ? 1 : k]);",
+     IP + "test_matches_numpy_brute_force"),
 ]
 
 
@@ -232,7 +278,7 @@ def _copy(dst, source):
 def _run_pins(cwd, pins):
     env = dict(os.environ, OMP_NUM_THREADS="2")
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
-    cmd += [f"tests/test_oracle_pins.py::{p}" for p in pins]
+    cmd += [f"tests/{p}" if "::" in p else f"tests/test_oracle_pins.py::{p}" for p in pins]
     return subprocess.run(cmd, cwd=cwd, env=env, capture_output=True, text=True, timeout=600)
 
 
