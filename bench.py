@@ -51,6 +51,17 @@ FLOP_PER_PAIR = 30
 BYTES_PER_PARTICLE = 200
 BYTES_PER_EVALUATION = 80
 KNN_METRIC = "kNN SPH particles/s (h = K-th neighbour distance, rho at h)"
+INTERACT_METRIC = "SPH interaction-pass particles/s (rho, velocity mean, dispersion, div, curl at h)"
+# FP32 operations per in-h pair of the interaction pass (FMA = 2): the distance test (3
+# differences, r^2: 1 mul + 2 FMA), q (1 mul, sqrt), w and g = -w'/q (7), u = v_j - v_i (3),
+# m w and m g (2), S0 (1), S1 (3 FMA), |u|^2 (1 mul + 2 FMA) and S2 (1 FMA), d . u (1 mul + 2
+# FMA) and D (1 FMA), d x u (3 mul + 3 FMA) and C (3 FMA)
+FLOP_PER_INTERACT_PAIR = 58
+# algorithmic HBM bytes per particle of one interaction call: the velocity gather (24 B read,
+# 16 B record written), the solve set-up (h read, sorted h, FP32 h, todo: 28 B), the target's
+# position record, velocity record and FP64 velocity (16 + 16 + 24 B) and the outputs (9
+# doubles + a count: 76 B)
+BYTES_PER_INTERACT_PARTICLE = 200
 # one neighbour-list entry: a squared distance from three offsets (3 subtractions, 3 multiplies,
 # 2 additions); the radius compare and the selection are not counted
 FLOP_PER_LIST_ENTRY = 8
@@ -72,6 +83,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
     ap.add_argument("--kernel", default="m4", choices=["m4", "c6"],
                     help="c6: the paper's Wendland C6 kernel at Nngb = 295 +- 5")
+    ap.add_argument("--interact", action="store_true",
+                    help="time the interaction pass (sph_interact: velocity mean, dispersion, "
+                         "divergence and curl at the converged h) instead of the solve")
     ap.add_argument("--knn", type=int, default=0,
                     help="K > 0: time the k-nearest-neighbour h (sph_knn_solve) instead of the "
                          "N_w solve; the paper's K is 295")
@@ -213,6 +227,26 @@ def cpu_baseline_knn(wl, n_targets, k, kernel="m4"):
     return {"value": len(tg) / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{len(tg):,} random targets of the same workload, K = {k}: every distance to "
                       f"all {wl.n:,} particles sorted (qsort), then rho at h (FP64, OpenMP over "
+                      f"targets); {dt:.1f} s wall",
+            "seconds": dt}
+
+
+def cpu_baseline_interact(wl, vel, h, n_targets=32):
+    """The oracle's interaction sums on sampled targets of the same workload at the GPU's h, by
+    brute force over all particles (a grid over tens of millions of particles costs a sort per
+    level).  The oracle hands targets to its threads in chunks of 16."""
+    import numpy as np
+
+    import oracle
+
+    k = min(n_targets, wl.n)
+    tg = np.sort(np.random.default_rng(97).choice(wl.n, size=k, replace=False))
+    t0 = time.perf_counter()
+    oracle.interact(wl.pos, wl.mass, vel, h[tg], box=wl.box, periodic=wl.periodic, targets=tg, mode="brute")
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": min(oracle.threads(), -(-k // 16)), "kind": "oracle",
+            "sample": f"{k} random targets of the same workload at the GPU's converged h: neighbours by "
+                      f"brute force over all {wl.n:,} particles, then the sums (FP64, OpenMP over "
                       f"targets); {dt:.1f} s wall",
             "seconds": dt}
 
@@ -753,6 +787,182 @@ def run_knn(args):
         dist.destroy_process_group()
 
 
+def run_interact(args):
+    """The interaction pass: one step = sph_interact over every particle of the workload at its
+    converged h (solved once, untimed): velocity records, work items and the interaction kernel
+    (velocity mean, dispersion, divergence and curl over the neighbours of Eq. 1)."""
+    import numpy as np
+    import torch
+
+    from paper_1612_06090_gb300 import binding as B
+    from paper_1612_06090_gb300 import inputs
+
+    rank, world = dist_init(args)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl, desc = workload(args)
+    n = wl.n
+    kern = B.SPH_KERNEL_WENDLAND_C6 if args.kernel == "c6" else B.SPH_KERNEL_M4
+    stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
+    vel_np = inputs.velocities(wl.pos, inputs.CONFIG_SEEDS[args.config] + 100)
+    gen_s = time.perf_counter() - t_gen
+    pos = torch.as_tensor(wl.pos, device=dev)
+    mass = torch.as_tensor(wl.mass, device=dev)
+    vel = torch.as_tensor(vel_np, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    out = {"rho": torch.empty(n, dtype=torch.float64, device=dev),
+           "vmean": torch.empty((3, n), dtype=torch.float64, device=dev),
+           "sigma2": torch.empty(n, dtype=torch.float64, device=dev),
+           "div": torch.empty(n, dtype=torch.float64, device=dev),
+           "curl": torch.empty((3, n), dtype=torch.float64, device=dev),
+           "count": torch.empty(n, dtype=torch.int32, device=dev)}
+
+    def make(prec):
+        s = B.Solver(n, stream=stream, precision=prec, box=wl.box, nngb=wl.nngb, tol=wl.tol, kernel=kern,
+                     use_graph=True)
+        s.sort(pos, mass)
+        return s
+
+    s32 = make(B.SPH_PREC_FP32_KAHAN)
+    r = s32.solve(torch.as_tensor(wl.h0, device=dev))
+    if r["status"] != B.SPH_OK:
+        raise B.SphError(r["status"], "the untimed solve did not converge")
+    h = r["h"]
+
+    def step(s, hh, vv, stats_out=None):
+        stats = B.SphStats()
+        st = B.sph_interact(s.ctx, hh.data_ptr(), vv.data_ptr(), out["rho"].data_ptr(), out["vmean"].data_ptr(),
+                            out["sigma2"].data_ptr(), out["div"].data_ptr(), out["curl"].data_ptr(),
+                            out["count"].data_ptr(), stats)
+        if st != B.SPH_OK:
+            raise B.SphError(st, B.sph_last_error(s.ctx))
+        if stats_out is not None:
+            stats_out.append(stats.to_dict())
+
+    def timed(s, steps, warmup):
+        for _ in range(warmup):
+            step(s, h, vel)
+        torch.cuda.synchronize()
+        stats = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(s, h, vel, stats)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return [a.elapsed_time(b) for a, b in ev], stats, time.perf_counter() - w0
+
+    with ClockSampler(local) as clk:
+        ms32, st32, wall32 = timed(s32, args.steps, args.warmup)
+    clocks = clk.summary()
+    t_max = max_over_ranks(statistics.mean(ms32), world)
+    value = world * n / (t_max / 1e3)
+    res32 = {k: v.cpu().numpy() for k, v in out.items()}
+
+    peak_tflops, probe = probe_fp32_peak(stream.cuda_stream)
+    k_ms = sum(s_["density_ms"] for s_ in st32) / max(1, len(st32))
+    pairs = sum(s_["pair_evals"] for s_ in st32) // max(1, len(st32))
+    achieved = pairs * FLOP_PER_INTERACT_PAIR / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_gbs = BYTES_PER_INTERACT_PARTICLE * n / (t_max / 1e3) / 1e9
+    roof = {"bound": "alu", "kernel": "k_interact<FP32> (item set-up + staging + pair sums)",
+            "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_note": "measured: dependent-FMA probe (libsph_probe.so), timed alone with CUDA events",
+            "peak_probe": probe, "flop_per_pair": FLOP_PER_INTERACT_PAIR, "pairs_per_step": pairs,
+            "candidate_tests_per_step": sum(s_["pair_tests"] for s_ in st32) // max(1, len(st32)),
+            "kernel_ms_per_step": k_ms, "kernel_timing": "CUDA events around work-item set-up and the "
+            "interaction kernel inside each call", "kernel_share_of_step": k_ms / max(1e-9, t_max),
+            "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": hbm_gbs / hbm_peak,
+            "hbm_note": f"algorithmic bytes {BYTES_PER_INTERACT_PARTICLE} B per particle over the step time; "
+                        "peak = measured copy bandwidth (MEASURED_PEAKS.json)"}
+    launches = sum(s_["kernel_launches"] for s_ in st32)
+
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = make(B.SPH_PREC_FP64)
+        ms64, _, _ = timed(s64, args.fp64_steps, 1)
+        t64 = max_over_ranks(statistics.mean(ms64), world)
+        res64 = {k: v.cpu().numpy() for k, v in out.items()}
+        sc = np.sqrt(np.maximum(res64["sigma2"], 0.0)) + 1e-300
+        fp64 = {"value": world * n / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64,
+                "fp32_vs_fp64": {"max_rel_rho_err": float(np.max(np.abs(res32["rho"] / res64["rho"] - 1.0))),
+                                 "count_equal_frac": float(np.mean(res32["count"] == res64["count"])),
+                                 "median_rel_sigma2_err": float(np.median(np.abs(res32["sigma2"] - res64["sigma2"])
+                                                                          / (sc * sc))),
+                                 "median_abs_vmean_err_over_sigma": float(np.median(
+                                     np.max(np.abs(res32["vmean"] - res64["vmean"]), axis=0) / sc))}}
+        s64.close()
+
+    e2e = None
+    if not args.no_e2e:
+        hp = {"h": h.cpu().pin_memory(), "vel": torch.as_tensor(vel_np).pin_memory()}
+        outp = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+        dh, dvel = torch.empty_like(h), torch.empty_like(vel)
+
+        def e2e_step():
+            dh.copy_(hp["h"], non_blocking=True)
+            dvel.copy_(hp["vel"], non_blocking=True)
+            step(s32, dh, dvel)
+            for k in out:
+                outp[k].copy_(out[k], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier(world)
+        te = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": world * n / te, "unit": UNIT, "ms_per_step": te * 1e3,
+               "h2d_bytes_per_step": n * (8 + 24), "d2h_bytes_per_step": n * (9 * 8 + 4),
+               "path": "pinned host h and velocities -> sph_interact on the sorted positions -> rho, "
+                       "vmean, sigma2, div, curl, count back to pinned host memory; wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline_interact(wl, vel_np, h.cpu().numpy(), args.cpu_sample or 32)
+        cpu.pop("seconds", None)
+    s32.close()
+    if rank == 0:
+        st0 = st32[-1]
+        line = {
+            "metric": INTERACT_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc + "; velocities: smooth periodic flow (6 Fourier modes, rms 1) + "
+                       "N(0, 0.3^2) per component", "n": n,
+                       "precision": "FP32 offsets, velocities and pair terms, Kahan sums, FP64 outputs",
+                       "h": "converged h of an untimed FP32 solve of the same workload",
+                       "l2": "inputs (positions, velocities) larger than L2, and L2 flushed between steps "
+                             "(256 MiB write, outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "velocity_generation_s": gen_s, "solve_ms": st0["solve_ms"],
+                       "wall_s_timed_region": wall32},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_gpu": fp64,
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
 def profiled_traffic():
     """Mean DRAM bytes per density pass from the committed ncu summary, valid only while the
     kernel sources are the ones that summary was captured from (else None)."""
@@ -1202,6 +1412,8 @@ def main():
         run_reference(args)
     elif args.knn:
         run_knn(args)
+    elif args.interact:
+        run_interact(args)
     elif args.config == "c4":
         run_batch(args)
     elif args.config == "c5":

@@ -226,6 +226,31 @@ sph_status sph_neighbours_sampled(sph_ctx *ctx, const double *h_dev, int64_t n_s
                                   const int64_t *sample_dev, int32_t max_nbr, int32_t *nbr_dev,
                                   int32_t *nbr_count_dev, double *rho_out_dev, int32_t *count_out_dev);
 
+/* Further pair computations over the same neighbour sets: the "other particle interaction
+ * computations" that Listing 1 runs inside the density loop after the density sum (the second
+ * phase of the particle interactions, Sec. II-A).  The paper leaves them open; these are the
+ * standard SPH velocity-field estimates, in gather form at each particle's h (typically the
+ * converged h of sph_density_solve), over j with r_ij < h_i, the particle itself included:
+ *   rho_i      = sum_j m_j W_ij                                  (Eq. 1)
+ *   vmean_i    = (1 / rho_i) sum_j m_j W_ij v_j                  kernel-weighted mean velocity
+ *   sigma2_i   = (1 / rho_i) sum_j m_j W_ij |v_j - vmean_i|^2    velocity dispersion
+ *   div_i      = (1 / rho_i) sum_j m_j (v_j - v_i) . grad_i W_ij
+ *   curl_i     = (1 / rho_i) sum_j m_j (v_i - v_j) x grad_i W_ij
+ * with W_ij = W(r_ij, h_i) and grad_i W_ij = dW/dr(r_ij) (r_i - r_j) / r_ij (zero at r = 0).
+ *   h_dev:             n doubles, caller order, each in (0, min(box)/2) when periodic;
+ *   vel_xyz_dev:       3 x n doubles, caller order (x block, y block, z block);
+ *   rho_out_dev, sigma2_out_dev, div_out_dev: n doubles; vmean_xyz_out_dev, curl_xyz_out_dev:
+ *                      3 x n doubles (x, y, z blocks); count_out_dev: n int32 (#{r_ij < h_i});
+ *   stats (nullable):  passes = 1, pair_evals (in-h pairs), pair_tests, solve_ms (the call) and
+ *                      density_ms (work-item set-up and the interaction kernel).
+ * FP64 precision: the neighbour test and every pair term in FP64 from the FP64 positions and
+ * velocities.  FP32_KAHAN: FP32 offsets, velocities and pair terms with compensated sums.
+ * Uses context memory only (32 bytes of velocity records per particle of capacity).
+ * Errors: INVALID_ARG (NULL), NOT_SORTED, DEVICE_STATUS (bad h, non-finite velocity), CUDA. */
+sph_status sph_interact(sph_ctx *ctx, const double *h_dev, const double *vel_xyz_dev, double *rho_out_dev,
+                        double *vmean_xyz_out_dev, double *sigma2_out_dev, double *div_out_dev,
+                        double *curl_xyz_out_dev, int32_t *count_out_dev, sph_stats *stats);
+
 /* k-nearest-neighbour smoothing lengths: the Subfind form of the density loop (Sec. IV-D and
  * Listing 3), where each particle's neighbour list is put in order of distance and its K
  * nearest entries interact.  For every particle of the last sph_sort:

@@ -35,7 +35,7 @@ EXPORTED = ("sph_create", "sph_set_params", "sph_sort", "sph_density_solve", "sp
             "sph_knn_solve",
             "sph_batch_solve", "sph_destroy", "sph_status_string", "sph_last_error",
             "sph_density_eval_static", "sph_get_tuning", "sph_set_tuning", "sph_autotune",
-            "sph_neighbours_sampled")
+            "sph_neighbours_sampled", "sph_interact")
 SPH_STATIC_MAX_PARTICLES = 32768
 SPH_KNN_MAX_K = 512
 
@@ -153,6 +153,8 @@ def lib() -> ctypes.CDLL:
     L.sph_autotune.argtypes = [vp, vp, ctypes.POINTER(SphTuning)]
     L.sph_neighbours_sampled.restype = i32
     L.sph_neighbours_sampled.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, vp]
+    L.sph_interact.restype = i32
+    L.sph_interact.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SphStats)]
     L.sph_density_eval_static.restype = i32
     L.sph_density_eval_static.argtypes = [ctypes.POINTER(SphParams), i64, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = L
@@ -237,6 +239,14 @@ def sph_neighbours_sampled(ctx, h_ptr: int, n_sample: int, sample_ptr: int, max_
     return lib().sph_neighbours_sampled(ctypes.c_void_p(ctx), v(h_ptr), int(n_sample), v(sample_ptr),
                                         int(max_nbr), v(nbr_ptr), v(nbr_count_ptr), v(rho_ptr),
                                         v(count_ptr))
+
+
+def sph_interact(ctx, h_ptr: int, vel_xyz_ptr: int, rho_ptr: int, vmean_xyz_ptr: int, sigma2_ptr: int,
+                 div_ptr: int, curl_xyz_ptr: int, count_ptr: int, stats=None) -> int:
+    v = lambda p: ctypes.c_void_p(p or None)  # noqa: E731
+    return lib().sph_interact(ctypes.c_void_p(ctx), v(h_ptr), v(vel_xyz_ptr), v(rho_ptr), v(vmean_xyz_ptr),
+                              v(sigma2_ptr), v(div_ptr), v(curl_xyz_ptr), v(count_ptr),
+                              ctypes.byref(stats) if stats is not None else None)
 
 
 def sph_batch_solve(ctx, n_groups: int, offsets_ptr: int, pos_xyz_ptr: int, mass_ptr: int,
@@ -433,6 +443,29 @@ class Solver:
         self._check(sph_density_eval(self.ctx, h.data_ptr(), rho.data_ptr(), count.data_ptr(),
                                      nw.data_ptr(), dnw.data_ptr()))
         return {"rho": rho, "nw": nw, "dnw": dnw, "count": count}
+
+    def interact(self, h, vel):
+        """Velocity mean, dispersion, divergence and curl over each particle's neighbours at its
+        h (the further pair computations of the density loop).  vel: (3, n) float64.  Returns
+        rho, vmean (3, n), sigma2, div, curl (3, n), count (int32) and the call's stats."""
+        torch = self._torch
+        vshape = (3, self.n) if self.n > 0 else None
+        for cuda in (False, True):  # types and shapes of both first, then their device
+            self._per_particle(h, "h", cuda=cuda)
+            check_tensor(vel, "vel", torch.float64, vshape, self.device, ndim=2, cuda=cuda)
+        h = h.contiguous()
+        vel = vel.contiguous()
+        rho = torch.empty_like(h)
+        sigma2 = torch.empty_like(h)
+        div = torch.empty_like(h)
+        vmean = torch.empty_like(vel)
+        curl = torch.empty_like(vel)
+        count = torch.empty(h.shape[0], dtype=torch.int32, device=h.device)
+        stats = SphStats()
+        self._check(sph_interact(self.ctx, h.data_ptr(), vel.data_ptr(), rho.data_ptr(), vmean.data_ptr(),
+                                 sigma2.data_ptr(), div.data_ptr(), curl.data_ptr(), count.data_ptr(), stats))
+        return {"rho": rho, "vmean": vmean, "sigma2": sigma2, "div": div, "curl": curl, "count": count,
+                "stats": stats.to_dict()}
 
     def neighbours(self, h, sample, max_nbr):
         """Neighbour sets of the sampled particles at fixed h (one density evaluation that also

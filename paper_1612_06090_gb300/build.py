@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(HERE, "libsph.so")
 PROBE_PATH = os.path.join(HERE, "libsph_probe.so")
 
 SOURCES = ["sph_scan.cu", "sph_sort.cu", "sph_density.cu", "sph_knn.cu", "sph_solve.cu", "sph_capi.cu",
-           "sph_static_eval.cu"]
+           "sph_static_eval.cu", "sph_interact.cu"]
 PROBE_SOURCES = ["sph_probe.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("sph_common.cuh", "sph_kernels.cuh", "sph_items.cuh")] + [
     os.path.join(INCLUDE, "sph.h"), os.path.join(INCLUDE, "sph_probe.h")]

@@ -51,6 +51,7 @@ struct sph_ctx {
     int32_t *nb_slot = nullptr;  // neighbour export: caller index -> sample row
     int32_t *lst = nullptr, *lst_n = nullptr, *todo_s = nullptr;  // cached neighbour lists
     double *lst_r = nullptr;
+    void *vrec = nullptr;  // sorted velocities of the interaction pass (32 bytes a particle)
     float *h32 = nullptr, *e_rho32 = nullptr, *e_nw32 = nullptr, *e_dnw32 = nullptr;
     DevState *ds = nullptr;
 
@@ -185,6 +186,7 @@ size_t carve(sph_ctx *c, char *base)
     c->lst_n = le > 0 ? (int32_t *)take(cap * 4) : nullptr;
     c->lst_r = le > 0 ? (double *)take(cap * 8) : nullptr;
     c->todo_s = le > 0 ? (int32_t *)take(cap * 4) : nullptr;
+    c->vrec = take((size_t)cap * 32);
     c->ds = (DevState *)take(sizeof(DevState));
     return off;
 }
@@ -355,6 +357,7 @@ sph_status device_status_error(sph_ctx *c, int bits)
     if (bits & kBadH) what += " h not in (0, min(box)/2) or bad group nngb/tol;";
     if (bits & 8) what += " internal cell-count guard;";
     if (bits & kBadSample) what += " sample index outside [0, n) or repeated;";
+    if (bits & kBadVelocity) what += " non-finite velocity;";
     return fail(c, SPH_ERR_DEVICE_STATUS, "device flagged the input:%s", what.c_str());
 }
 
@@ -911,6 +914,65 @@ sph_status sph_neighbours_sampled(sph_ctx *ctx, const double *h_dev, int64_t n_s
     s = read_state(ctx);
     if (s != SPH_OK) return s;
     if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    return SPH_OK;
+}
+
+sph_status sph_interact(sph_ctx *ctx, const double *h_dev, const double *vel_xyz_dev, double *rho_out_dev,
+                        double *vmean_xyz_out_dev, double *sigma2_out_dev, double *div_out_dev,
+                        double *curl_xyz_out_dev, int32_t *count_out_dev, sph_stats *stats)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!h_dev || !vel_xyz_dev || !rho_out_dev || !vmean_xyz_out_dev || !sigma2_out_dev || !div_out_dev ||
+        !curl_xyz_out_dev || !count_out_dev)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "NULL pointer argument");
+    if (!ctx->sorted) return fail(ctx, SPH_ERR_NOT_SORTED, "sph_sort has not run on this context");
+    cudaStream_t st = ctx->stream;
+    const int launches0 = ctx->launches;
+    SolveArgs a = solve_args(ctx);
+    a.lst = nullptr;  // one pass, searched
+    CU(ctx, cudaEventRecord(ctx->ev[2], st), "event");
+    CU(ctx, cudaMemsetAsync(&ctx->ds->status, 0, sizeof(int32_t), st), "clearing the status word");
+    CU(ctx, cudaMemsetAsync(&ctx->ds->h_varies, 0, sizeof(int32_t), st), "clearing the h flag");
+    CU(ctx, launch_solve_init(a, h_dev, 1, st), "init");
+    CU(ctx, launch_gather_vel(a, vel_xyz_dev, ctx->vrec, st), "velocity records");
+    sph_status s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status | ctx->ds_host->sort_status)
+        return device_status_error(ctx, ctx->ds_host->status | ctx->ds_host->sort_status);
+    InteractArgs ia{};
+    ia.vrec = ctx->vrec;
+    ia.vel = vel_xyz_dev;
+    ia.rho = rho_out_dev;
+    ia.vmean = vmean_xyz_out_dev;
+    ia.sigma2 = sigma2_out_dev;
+    ia.div = div_out_dev;
+    ia.curl = curl_xyz_out_dev;
+    ia.count = count_out_dev;
+    a.dens_ev[0] = ctx->dev_ev[0];
+    a.dens_ev[1] = ctx->dev_ev[1];
+    CU(ctx, launch_interact_pass(a, ia, st), "interaction pass");
+    CU(ctx, cudaEventRecord(ctx->ev[3], st), "event");
+    s = read_state(ctx);
+    if (s != SPH_OK) return s;
+    if (ctx->ds_host->status) return device_status_error(ctx, ctx->ds_host->status);
+    if (stats) {
+        const DevState &d = *ctx->ds_host;
+        *stats = sph_stats{};
+        stats->passes = 1;
+        stats->kernel_launches = ctx->launches - launches0;
+        stats->todo_per_pass[0] = ctx->n;
+        stats->pair_evals = (int64_t)d.pair_evals;
+        stats->pair_tests = (int64_t)d.pair_tests;
+        stats->pairs_per_pass[0] = (int64_t)d.pair_evals;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+        stats->solve_ms = ms;
+        if (cudaEventElapsedTime(&ms, ctx->dev_ev[0], ctx->dev_ev[1]) == cudaSuccess) {
+            stats->density_ms = ms;
+            stats->density_ms_per_pass[0] = ms;
+        }
+        stats->density_launches = 1;
+    }
     return SPH_OK;
 }
 

@@ -78,6 +78,7 @@ enum DevStatusBits : int32_t {
     kBadMass = 2,       // mass not finite or <= 0
     kBadH = 4,          // h not finite, <= 0, or >= min(box)/2 when periodic
     kBadSample = 16,    // neighbour export: a sample index outside [0, n) or repeated
+    kBadVelocity = 32,  // interaction pass: a velocity component not finite
 };
 
 // ---------------------------------------------------------------------------------------

@@ -521,41 +521,8 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
                                 : hf * a.list_margin * (1.0f + 1e-5f);
         item_setup(S, a.kl, a.cell_div, active, P, hq, G3, rel);
         const float qf[3] = {(float)S.q[0], (float)S.q[1], (float)S.q[2]};
-        // FP32 offsets are taken from the centre of the targets' box rather than the first
-        // target: the largest offset a near-boundary pair needs is then half the box plus h,
-        // which bounds the rounding of the FP32 distance test.  The origin moves to the centre
-        // (X0 + cen) once per item, with the query bounds; the ball centre and the cells are
-        // found relative to the first target before the move.
-        float ccx, ccy, ccz, ball2;
-        const float cc0[3] = {0.5f * ((float)G3.bmin[0] + (float)G3.bmax[0]) * qf[0],
-                              0.5f * ((float)G3.bmin[1] + (float)G3.bmax[1]) * qf[1],
-                              0.5f * ((float)G3.bmin[2] + (float)G3.bmax[2]) * qf[2]};
-        {
-            const float qm = fmaxf(qf[0], fmaxf(qf[1], qf[2]));
-            float half2 = 0.f, c2[3];
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const float hx = 0.5f * (float)((int64_t)G3.bmax[d] - (int64_t)G3.bmin[d]) * qf[d];
-                half2 = fmaf(hx, hx, half2);
-                const int64_t sum = (int64_t)G3.bmin[d] + (int64_t)G3.bmax[d];
-                const int64_t cen = sum >> 1;
-                c2[d] = 0.5f * (float)(sum - 2 * cen) * qf[d];  // 0 or half a unit
-                // the wrapped 32-bit differences from the new origin are exact: the true
-                // offset of any candidate within h of a target of this item fits in 32 bits
-                G3.X0[d] += (uint32_t)cen;
-                rel[d] = (int32_t)((uint32_t)rel[d] - (uint32_t)cen);
-                if (!G3.full[d]) {
-                    const int64_t lo = G3.lo[d] - cen, hi = G3.hi[d] - cen;
-                    G3.qlo[d] = (int)(lo < INT_MIN ? (int64_t)INT_MIN : lo);
-                    G3.qhi[d] = (int)(hi > INT_MAX ? (int64_t)INT_MAX : hi);
-                }
-            }
-            ccx = c2[0];
-            ccy = c2[1];
-            ccz = c2[2];
-            const float Rm = (sqrtf(half2) + G3.hmax) * (1.0f + 1e-5f) + 8.0f * qm;
-            ball2 = Rm * Rm;
-        }
+        const ItemBall B = item_recentre(G3, rel, qf);
+        const float ccx = B.cc[0], ccy = B.cc[1], ccz = B.cc[2], ball2 = B.ball2;
         L.tx = (float)rel[0] * qf[0];
         L.ty = (float)rel[1] * qf[1];
         L.tz = (float)rel[2] * qf[2];
@@ -590,12 +557,8 @@ __global__ void __launch_bounds__(kThreads, kMode >= 2 ? 3 : 2)
             if (lane == 0) atomicOr(&a.ds->status, 8);
             continue;
         }
-        // A candidate can lie within h of some target only inside the ball around the
-        // centre of the targets' box of radius (half-diagonal + h_max); staging keeps the
-        // box test (exact, integer) and adds this ball test (FP32 with a margin that covers
-        // the rounding of the offsets and the fixed-point quantisation).
         long long rr[2];
-        item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, cc0, ball2, qf, rr);
+        item_ranges(G3, g, S, a.kl, a.ctab, a.key, ncell, B.cc0, ball2, qf, rr);
 
         Acc32 A32 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
         Acc64 A64 = {0.0, 0.0, 0.0, 0};

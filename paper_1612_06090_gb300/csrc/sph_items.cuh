@@ -126,6 +126,51 @@ __device__ __forceinline__ void item_setup(const SegInfo &S, const KeyLayout &kl
     }
 }
 
+// The staging geometry of an item in FP32 offset units.  The ball around the centre of the
+// targets' box, of radius (half-diagonal + h_max), holds every candidate within h of some
+// target; staging keeps the exact integer box test and adds this ball test (FP32, with a margin
+// that covers the rounding of the offsets and the fixed-point quantisation).
+// FP32 offsets are taken from the centre of the targets' box rather than the first target:
+// the largest offset a near-boundary pair needs is then half the box plus h, which bounds the
+// rounding of the FP32 distance test.  The origin moves to the centre (X0 + cen) once per item,
+// with the query bounds and the targets' offsets `rel`; cc0 (the ball centre relative to the
+// first target, for the cell culling) is found before the move, cc (relative to the new
+// origin: 0 or half a unit per dimension) after it.
+struct ItemBall {
+    float cc0[3];
+    float cc[3];
+    float ball2;
+};
+
+__device__ __forceinline__ ItemBall item_recentre(ItemGeom &G, int rel[3], const float qf[3])
+{
+    ItemBall B;
+#pragma unroll
+    for (int d = 0; d < 3; d++) B.cc0[d] = 0.5f * ((float)G.bmin[d] + (float)G.bmax[d]) * qf[d];
+    const float qm = fmaxf(qf[0], fmaxf(qf[1], qf[2]));
+    float half2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const float hx = 0.5f * (float)((int64_t)G.bmax[d] - (int64_t)G.bmin[d]) * qf[d];
+        half2 = fmaf(hx, hx, half2);
+        const int64_t sum = (int64_t)G.bmin[d] + (int64_t)G.bmax[d];
+        const int64_t cen = sum >> 1;
+        B.cc[d] = 0.5f * (float)(sum - 2 * cen) * qf[d];  // 0 or half a unit
+        // the wrapped 32-bit differences from the new origin are exact: the true offset of any
+        // candidate within h of a target of this item fits in 32 bits
+        G.X0[d] += (uint32_t)cen;
+        rel[d] = (int32_t)((uint32_t)rel[d] - (uint32_t)cen);
+        if (!G.full[d]) {
+            const int64_t lo = G.lo[d] - cen, hi = G.hi[d] - cen;
+            G.qlo[d] = (int)(lo < INT_MIN ? (int64_t)INT_MIN : lo);
+            G.qhi[d] = (int)(hi > INT_MAX ? (int64_t)INT_MAX : hi);
+        }
+    }
+    const float Rm = (sqrtf(half2) + G.hmax) * (1.0f + 1e-5f) + 8.0f * qm;
+    B.ball2 = Rm * Rm;
+    return B;
+}
+
 // Ranges of the item's cells; lane holds cells lane + 32 k, k < K.  A cell that lies
 // entirely outside the staging ball (centre cc, squared radius ball2, both in the FP32 offset
 // units of the item) can hold no candidate, so its range is left empty: no lookup, no loads.

@@ -110,6 +110,18 @@ struct SolveArgs {
     float list_margin;         // > 1
 };
 
+// Buffers of the interaction pass (sph_interact.cu).
+struct InteractArgs {
+    const void *vrec;   // sorted velocities: float4 {vx, vy, vz, 0} (FP32 mode) or double4_32a
+    const double *vel;  // caller velocities, 3 x n (x block, y block, z block)
+    double *rho;        // outputs in caller order (vmean, curl: 3 x n)
+    double *vmean;
+    double *sigma2;
+    double *div;
+    double *curl;
+    int32_t *count;
+};
+
 cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_iter, cudaStream_t st);
 // One evaluation pass over todo[cur]; when `update`, also the h update and the next todo
 // list (todo[1 - cur]).
@@ -134,6 +146,12 @@ cudaError_t launch_knn_pass(const SolveArgs &a, int cur, int k, cudaStream_t st)
 cudaError_t launch_knn_finish(const SolveArgs &a, cudaStream_t st);
 // starting radii of the kNN passes (entries <= 0 are estimated from the cell tables)
 cudaError_t launch_knn_init(const SolveArgs &a, const double *h_in, int max_iter, int k, cudaStream_t st);
+// sph_interact.cu: the interaction kernel over the items of todo, and the sorted velocity
+// records (status bit kBadVelocity for a non-finite component)
+cudaError_t launch_interact(const SolveArgs &a, const InteractArgs &ia, const int32_t *todo, cudaStream_t st);
+cudaError_t launch_gather_vel(const SolveArgs &a, const double *vel, void *vrec, cudaStream_t st);
+// sph_solve.cu: one interaction pass over every particle (after launch_solve_init with one pass)
+cudaError_t launch_interact_pass(const SolveArgs &a, const InteractArgs &ia, cudaStream_t st);
 // neighbour export set-up: nb_slot (caller order, n entries) = -1 except nb_slot[sample[k]] = k;
 // counts zeroed; an index outside [0, n) or repeated sets kBadSample in the status word
 cudaError_t launch_nb_setup(const SolveArgs &a, int32_t *nb_slot, const int64_t *sample, int64_t n_sample,

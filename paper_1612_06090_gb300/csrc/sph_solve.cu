@@ -487,6 +487,18 @@ int blocks_for(int64_t n, int cap)
 
 }  // namespace
 
+// Work items of the dens_count entries of todo: head flags, then their positions.
+cudaError_t launch_items(const SolveArgs &a, const int32_t *todo, cudaStream_t st)
+{
+    const int grid = blocks_for(a.n, a.grid_cap);
+    if (a.item_cap > 0) k_item_flags_capped<<<grid, kCapTile, 0, st>>>(a, todo);
+    else k_item_flags<<<grid, kThreads, 0, st>>>(a, todo);
+    if (a.launches) *a.launches += 1;
+    // item starts = positions of the head flags
+    return compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->dens_count, &a.ds->n_items, a.scan_aux,
+                       a.grid_cap, st, a.launches);
+}
+
 cudaError_t launch_solve_init(const SolveArgs &a, const double *h_in, int max_iter, cudaStream_t st)
 {
     k_solve_init<<<blocks_for(a.n, a.grid_cap), kThreads, 0, st>>>(a, h_in, max_iter);
@@ -513,12 +525,7 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
         if (e != cudaSuccess) return e;
         stodo = a.todo_s;
     }
-    if (a.item_cap > 0) k_item_flags_capped<<<grid, kCapTile, 0, st>>>(a, stodo);
-    else k_item_flags<<<grid, kThreads, 0, st>>>(a, stodo);
-    if (a.launches) *a.launches += 1;
-    // item starts = positions of the head flags
-    e = compact_i32(a.flags, nullptr, a.items, nullptr, a.n, &a.ds->dens_count, &a.ds->n_items, a.scan_aux,
-                    a.grid_cap, st, a.launches);
+    e = launch_items(a, stodo, st);
     if (e != cudaSuccess) return e;
     e = launch_density(a, stodo, st);
     if (e != cudaSuccess) return e;
@@ -531,6 +538,19 @@ cudaError_t launch_pass(const SolveArgs &a, int cur, bool update, cudaStream_t s
     if (e != cudaSuccess) return e;
     k_pass_end<<<1, 1, 0, st>>>(a.ds);
     if (a.launches) *a.launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interact_pass(const SolveArgs &a, const InteractArgs &ia, cudaStream_t st)
+{
+    k_pass_begin<<<1, 1, 0, st>>>(a.ds, 0);
+    if (a.launches) *a.launches += 1;
+    cudaError_t e = launch_items(a, a.todo[0], st);
+    if (e != cudaSuccess) return e;
+    if (a.dens_ev[0]) cudaEventRecord(a.dens_ev[0], st);
+    e = launch_interact(a, ia, a.todo[0], st);
+    if (e != cudaSuccess) return e;
+    if (a.dens_ev[1]) cudaEventRecord(a.dens_ev[1], st);
     return cudaGetLastError();
 }
 

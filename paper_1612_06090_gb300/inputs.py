@@ -1,6 +1,7 @@
 """Seeded synthetic particle sets for the SPH density / smoothing-length solve.
 
-This module only draws positions, masses and starting smoothing lengths.  It holds
+This module only draws positions, masses, starting smoothing lengths and (for the
+interaction pass) velocities.  It holds
 none of the method's arithmetic (no kernel, no neighbour search, no h update), so both
 the CUDA path and the FP64 oracle may take their inputs from it.
 
@@ -38,6 +39,7 @@ __all__ = [
     "clumpy_snapshots",
     "clumpy_snapshot_series",
     "make",
+    "velocities",
     "mean_density_h",
     "CONFIG_SEEDS",
 ]
@@ -362,6 +364,39 @@ def clumpy_snapshots(snapshot: int = 0, **kw) -> Workload:
         wl.meta["n_snapshots"] = n_snap
         return wl
     raise ValueError(f"snapshot {snapshot} outside the series")
+
+
+def velocities(pos: np.ndarray, seed: int, bulk: float = 1.0, sigma: float = 0.3, n_modes: int = 6,
+               kmax: int = 3) -> np.ndarray:
+    """Seeded synthetic velocities for the interaction pass, (3, N) float64.
+
+    A smooth periodic flow, sum of n_modes Fourier modes a_m sin(2 pi k_m . x + phi_m) with
+    integer wave vectors |k_m,d| <= kmax (continuous across the periodic faces of the unit
+    box) and amplitudes N(0, bulk^2 / n_modes) per component, plus independent N(0, sigma^2)
+    per component and particle (the local dispersion).  The stream of draws depends on seed
+    only.
+    """
+    rng = np.random.default_rng(np.random.PCG64([seed, 23]))
+    k = rng.integers(-kmax, kmax + 1, size=(n_modes, 3)).astype(np.float64)
+    k[np.all(k == 0, axis=1), 0] = 1.0
+    amp = rng.normal(0.0, bulk / math.sqrt(n_modes), size=(n_modes, 3))
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=(n_modes, 3))
+    n = pos.shape[1]
+    vel = np.empty((3, n))
+
+    def one(c0):
+        c1 = min(n, c0 + _CHUNK)
+        x = pos[:, c0:c1]
+        g = np.random.default_rng(np.random.PCG64([seed, 29, c0 // _CHUNK]))
+        out = g.normal(0.0, sigma, size=(3, c1 - c0))
+        for m in range(n_modes):
+            arg = 2.0 * math.pi * (k[m] @ x)
+            for d in range(3):
+                out[d] += amp[m, d] * np.sin(arg + phase[m, d])
+        vel[:, c0:c1] = out
+
+    _parallel(one, range(0, n, _CHUNK))
+    return vel
 
 
 def make(config: str, **kw):

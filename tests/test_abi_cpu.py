@@ -135,6 +135,7 @@ def test_calls_on_null_context(B):
     assert B.sph_batch_solve(None, 1, 1, 1, 1, 1, 1, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
     assert B.sph_knn_solve(None, 64, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
     assert B.sph_set_params(None, B.make_params()) == B.SPH_ERR_INVALID_ARG
+    assert B.sph_interact(None, 1, 1, 1, 1, 1, 1, 1, 1) == B.SPH_ERR_INVALID_ARG
     B.sph_destroy(None)
 
 
@@ -179,6 +180,9 @@ def test_binding_rejects_tensors_the_library_would_misread(B):
         (lambda: s.knn(4, torch.ones(n, dtype=f32)), TypeError),
         (lambda: s.knn(4, torch.ones(2, n, dtype=f64)), ValueError),
         (lambda: s.autotune(torch.ones(n, dtype=f32)), TypeError),
+        (lambda: s.interact(torch.ones(n, dtype=f64), torch.zeros(3, n, dtype=f32)), TypeError),
+        (lambda: s.interact(torch.ones(n, dtype=f64), torch.zeros(n, 3, dtype=f64)), ValueError),
+        (lambda: s.interact(torch.ones(n - 1, dtype=f64), torch.zeros(3, n, dtype=f64)), ValueError),
         (lambda: s.batch_solve(torch.tensor([0, n], dtype=torch.int32), torch.zeros(3, n, dtype=f64),
                                torch.ones(n, dtype=f64), torch.ones(n, dtype=f64),
                                torch.ones(1, dtype=f64), torch.ones(1, dtype=f64)), TypeError),
