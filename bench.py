@@ -516,8 +516,8 @@ def run_native(args):
     achieved = pairs * FLOP_PER_PAIR / (dens_ms / 1e3) / 1e12 if dens_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_density<2> (FP32 pair loop)", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": profiled_traffic() if args.config == "c2" and not args.n and args.kernel == "m4" else None,
-            "traffic_note": "mean DRAM bytes per density pass (ncu, profiles/density_fp32_c2_1M.md)",
+            "traffic": None,
+            "traffic_note": "no ncu capture of this configuration is kept; the default c5 replay line carries one",
             "peak_note": "measured: dependent-FMA probe (libsph_probe.so), timed alone with CUDA events",
             "peak_probe": probe,
             "flop_per_pair": FLOP_PER_PAIR, "pairs_per_step": pairs // max(1, len(st32)),
@@ -961,24 +961,6 @@ def run_interact(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
-
-
-def profiled_traffic():
-    """Mean DRAM bytes per density pass from the committed ncu summary, valid only while the
-    kernel sources are the ones that summary was captured from (else None)."""
-    import hashlib
-    import re
-
-    try:
-        text = open(os.path.join(ROOT, "profiles", "density_fp32_c2_1M.md")).read()
-        src = b"".join(open(os.path.join(ROOT, "paper_1612_06090_gb300", "csrc", f), "rb").read()
-                       for f in ("sph_density.cu", "sph_items.cuh", "sph_common.cuh"))
-        want = re.search(r"kernel_source_sha256_16: (\w+)", text).group(1)
-        if hashlib.sha256(src).hexdigest()[:16] != want:
-            return None
-        return int(re.search(r"traffic_bytes_per_pass: (\d+)", text).group(1))
-    except Exception:
-        return None
 
 
 def roofline_from(stats_list, peak, kernel):
