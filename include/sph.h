@@ -135,6 +135,10 @@ typedef struct {
                              a cell of edge up to 2h may hold targets far apart relative to their
                              h; a finer grouping keeps each item's staging ball near its
                              targets' own (-2..3)                                              */
+    int32_t sparse_item_max; /* item_max used while the todo list is sparse: 0 = item_max, else 1,
+                             2, 4, 8, 16 or 32.  Late in a solve the few targets left can carry h
+                             so large that one item streams 10^5 candidates while the rest of
+                             the GPU waits; smaller items let several warps share that work    */
 } sph_tuning;
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy default stream)

@@ -106,6 +106,7 @@ class SphTuning(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32),
         ("list_margin_pct", ctypes.c_int32),
         ("sparse_shift", ctypes.c_int32),
+        ("sparse_item_max", ctypes.c_int32),
     ]
 
     def to_dict(self) -> dict:

@@ -74,7 +74,7 @@ struct sph_ctx {
         sph_tuning tuning{};
         KeyLayout kl{};
     } graph_key;
-    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0, 10, 0};
+    sph_tuning tuning{0, 3, 1, 0, 0, 32, 256, 0, 10, 0, 0};
     int launches = 0;
     int sort_launches = 0;  // kernels of the last sort stage
     int grid_cap = 0;
@@ -257,6 +257,7 @@ SolveArgs solve_args(sph_ctx *c)
         a.block_threads = bt;
     }
     a.gmax = c->tuning.item_max;
+    a.gmax_sparse = c->tuning.sparse_item_max > 0 ? c->tuning.sparse_item_max : c->tuning.item_max;
     a.item_cap = c->tuning.item_cap;
     // cached neighbour lists (the FP32 per-lane queue of direct_pct > 0 records none)
     const bool lists = c->params.list_entries > 0 && (c->params.precision == SPH_PREC_FP64 || c->tuning.direct_pct == 0);
@@ -286,8 +287,9 @@ int table_level(int64_t n, int lmax, int extra)
 }
 
 // Autotuner cache: one line per result,
-// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs lm ss" (the sph_tuning fields
-// in order); the last matching line wins.
+// "<gpu>|<log2 n>|<periodic>|<precision> gs cd te dp ic im bt bs lm ss sm" (the sph_tuning
+// fields in order; a line without the last field leaves it at its default); the last matching
+// line wins.
 std::string cache_key(const sph_ctx *c, int64_t n)
 {
     int b = 0;
@@ -307,10 +309,11 @@ bool cache_lookup(const sph_ctx *c, int64_t n, sph_tuning *t)
     bool found = false;
     while (fgets(line, sizeof(line), f)) {
         sph_tuning x = c->tuning;
-        if (sscanf(line, "%299s %d %d %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div, &x.table_extra,
-                   &x.direct_pct, &x.item_cap, &x.item_max, &x.block_threads, &x.blocks_per_sm,
-                   &x.list_margin_pct, &x.sparse_shift) == 11 &&
-            key == k) {
+        x.sparse_item_max = 0;
+        const int got = sscanf(line, "%299s %d %d %d %d %d %d %d %d %d %d %d", k, &x.group_shift, &x.cell_div,
+                               &x.table_extra, &x.direct_pct, &x.item_cap, &x.item_max, &x.block_threads,
+                               &x.blocks_per_sm, &x.list_margin_pct, &x.sparse_shift, &x.sparse_item_max);
+        if ((got == 11 || got == 12) && key == k) {
             *t = x;
             found = true;
         }
@@ -324,9 +327,9 @@ void cache_store(const sph_ctx *c, int64_t n, const sph_tuning &t)
     if (c->tune_cache.empty()) return;
     FILE *f = fopen(c->tune_cache.c_str(), "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div,
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d\n", cache_key(c, n).c_str(), t.group_shift, t.cell_div,
             t.table_extra, t.direct_pct, t.item_cap, t.item_max, t.block_threads, t.blocks_per_sm,
-            t.list_margin_pct, t.sparse_shift);
+            t.list_margin_pct, t.sparse_shift, t.sparse_item_max);
     fclose(f);
 }
 
@@ -338,7 +341,9 @@ bool tuning_ok(const sph_tuning *t)
            (t->item_cap == 0 || (t->item_cap >= 2 && t->item_cap <= 64)) && pow2 &&
            (t->block_threads == 64 || t->block_threads == 128 || t->block_threads == 256) &&
            t->blocks_per_sm >= 0 && t->blocks_per_sm <= 32 && t->list_margin_pct >= 1 && t->list_margin_pct <= 100 &&
-           t->sparse_shift >= -2 && t->sparse_shift <= 3;
+           t->sparse_shift >= -2 && t->sparse_shift <= 3 &&
+           (t->sparse_item_max == 0 ||
+            (t->sparse_item_max <= 32 && (t->sparse_item_max & (t->sparse_item_max - 1)) == 0));
 }
 
 sph_status read_state(sph_ctx *c)
@@ -800,7 +805,7 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
     }
     const int mode = ctx->params.precision == SPH_PREC_FP64 ? 0 : 2;
     for (int round = 0; round < 2; round++) {
-        for (int knob = 0; knob < 8; knob++) {
+        for (int knob = 0; knob < 9; knob++) {
             if (knob == 6 && ctx->params.list_entries == 0) continue;  // no lists, no margin
             int vals[4];
             int nv = 0;
@@ -812,6 +817,7 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
             case 4: vals[0] = 128, vals[1] = 256, nv = 2; break;                           // block_threads
             case 6: vals[0] = 5, vals[1] = 10, vals[2] = 20, nv = 3; break;                // list_margin_pct
             case 7: vals[0] = -1, vals[1] = 0, vals[2] = 1, vals[3] = 2, nv = 4; break;    // sparse_shift
+            case 8: vals[0] = 0, vals[1] = 1, vals[2] = 4, nv = 3; break;                  // sparse_item_max
             default: {                                                                     // blocks_per_sm
                 const int bt = best.block_threads;
                 const int ti = bt == 64 ? 0 : bt == 128 ? 1 : 2;
@@ -831,7 +837,8 @@ sph_status sph_autotune(sph_ctx *ctx, const double *h_dev, sph_tuning *best_out)
                              : knob == 4 ? &t.block_threads
                              : knob == 5 ? &t.blocks_per_sm
                              : knob == 6 ? &t.list_margin_pct
-                                         : &t.sparse_shift;
+                             : knob == 7 ? &t.sparse_shift
+                                         : &t.sparse_item_max;
                 if (*field == vals[v]) continue;
                 *field = vals[v];
                 const float ms = time_one(t, &err);

@@ -73,6 +73,7 @@ struct SolveArgs {
     int grid_cap;
     int density_grid;          // persistent blocks of the density kernels
     int gmax;                  // targets per work item (<= 32)
+    int gmax_sparse;           // the same while the todo list is sparse (< 1/8 of the particles)
     int item_cap;              // 0: items follow the grouping level; else the coarsest octree
                                // cell (not coarser than that level) with <= item_cap todo targets
     int block_threads;         // threads per block of the density kernels (64, 128 or 256)

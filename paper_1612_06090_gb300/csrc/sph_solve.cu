@@ -201,8 +201,8 @@ __global__ void k_set_loop(cudaGraphConditionalHandle handle, const DevState *ds
     cudaGraphSetConditional(handle, ds->loop_flag ? 1u : 0u);
 }
 
-// Work-item heads: a new item starts at every multiple of gmax and around single-target
-// ("big") entries.  While the todo list is dense (at least 1/8 of the particles) consecutive
+// Work-item heads: a new item starts at every multiple of gmax (gmax_sparse once the todo list
+// is sparse) and around single-target ("big") entries.  While the todo list is dense (at least 1/8 of the particles) consecutive
 // targets stay together if they share an octree cell at the coarser of their two grouping
 // levels and those levels differ by at most one; once it is sparse they must have the same
 // level and share the cell at it (long runs of far-apart targets would otherwise stretch an
@@ -220,6 +220,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
     // (lane 0 works its own out); the loop bound is the warp's first entry, so shuffles see the
     // whole warp
     const int shift = dense ? a.group_shift : a.sparse_shift;
+    const int gm = dense ? a.gmax : a.gmax_sparse;
     for (int tb = blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < T; tb += gridDim.x * blockDim.x) {
         const int t = tb + lane;
         const bool have = t < T;
@@ -240,7 +241,7 @@ __global__ void k_item_flags(SolveArgs a, const int32_t *__restrict__ todo)
             bucket_of(kp, a.h32[pp], a.segs[seg_of(kp, a.kl)], a.kl, shift, lp, prep, bigp, ctab0, hmul);
         }
         if (!have) continue;
-        int head = (t % a.gmax == 0) || big;
+        int head = (t % gm == 0) || big;
         if (!head) {
             if (dense) {
                 const int m = lp < l ? lp : l;
@@ -286,7 +287,9 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
     __shared__ int sl[kCapTile + 1];  // entries base - 1 .. base + kCapTile - 1: level | big << 8
     const int T = a.ds->dens_count;
     const int cap = a.item_cap < kCapMax ? a.item_cap : kCapMax;
-    const int shift = 8 * (int64_t)T >= a.n ? a.group_shift : a.sparse_shift;
+    const bool dense = 8 * (int64_t)T >= a.n;
+    const int shift = dense ? a.group_shift : a.sparse_shift;
+    const int gm = dense ? a.gmax : a.gmax_sparse;
     const int32_t *ctab0 = a.ds->pass == 0 && a.kl.seg_bits > 0 ? a.ctab : nullptr;
     const int ntiles = (T + kCapTile - 1) / kCapTile;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(kCapTile) k_item_flags_capped(SolveArgs a, con
                 const int prev = sl[threadIdx.x];
                 const int lvl = me & 0xff;
                 head = (prev >> 8) != 0 || (prev & 0xff) != lvl || dprev(t) < lvl;
-                if (!head) head = from_start >= 0 ? from_start % a.gmax == 0 : t % a.gmax == 0;
+                if (!head) head = from_start >= 0 ? from_start % gm == 0 : t % gm == 0;
             }
             a.flags[t] = head;
         }

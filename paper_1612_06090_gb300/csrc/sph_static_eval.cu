@@ -255,6 +255,7 @@ extern "C" sph_status sph_density_eval_static(const sph_params *params, int64_t 
     a.kernel = SPH_KERNEL_M4;
     a.density_grid = dev->density_grid[params->precision == SPH_PREC_FP64 ? 0 : 1];
     a.gmax = 32;
+    a.gmax_sparse = 32;
     a.group_shift = 1;
     a.cell_div = 3;
     a.direct_pct = 0;
