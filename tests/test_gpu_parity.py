@@ -408,6 +408,62 @@ def test_autotune_picks_a_tuning_caches_it_and_keeps_results(tmp_path):
     assert open(cache).read().strip()
 
 
+@pytest.mark.parametrize("tuning", [
+    dict(item_max=8, sparse_item_max=1, sparse_shift=2),
+    dict(item_cap=16, group_shift=1, cell_div=2, sparse_item_max=4),
+    dict(item_cap=64, item_max=16, group_shift=-1, block_threads=128, sparse_shift=-1),
+])
+def test_tunings_keep_fp64_parity(tuning):
+    """Every tuning knob changes only how targets are grouped and launched: in FP64 the counts
+    stay exact and h, rho within 1e-12 of the oracle, for a periodic clustered set and for open
+    batch groups whose late passes are sparse."""
+    wl = inputs.make("c2", n=1 << 14)
+    s = B.Solver(wl.n, precision=FP64, box=wl.box)
+    s.set_tuning(**tuning)
+    s.sort(T(wl.pos), T(wl.mass))
+    r = s.solve(T(wl.h0))
+    torch.cuda.synchronize()
+    g = {k: (np_(v) if torch.is_tensor(v) else v) for k, v in r.items()}
+    s.close()
+    assert g["status"] == B.SPH_OK
+    o = oracle.solve(wl.pos, wl.mass, wl.h0, box=wl.box, nngb=wl.nngb, tol=wl.tol)
+    check_solve(wl.pos, wl.mass, wl.box, True, wl.nngb, wl.tol, g, o, np.arange(wl.n), rtol=1e-12,
+                delta=1e-9 * wl.nngb, max_mismatch_frac=1e-3, count_exact=True)
+    bw = inputs.plummer_groups(n_groups=40, nmin=32, nmax=5000, seed=32)
+    s = B.Solver(bw.n, precision=FP64)
+    s.set_tuning(**tuning)
+    r = s.batch_solve(T(bw.offsets, torch.int64), T(bw.pos), T(bw.mass), T(bw.h0), T(bw.nngb), T(bw.tol))
+    torch.cuda.synchronize()
+    gh, grho, gc = np_(r["h"]), np_(r["rho"]), np_(r["count"])
+    s.close()
+    o = oracle.batch_solve(bw.offsets, bw.pos, bw.mass, bw.h0, bw.nngb, bw.tol)
+    ok = (rel_err(gh, o["h"]) <= 1e-12) & (rel_err(grho, o["rho"]) <= 1e-12)
+    assert ok.mean() >= 0.998
+    np.testing.assert_array_equal(gc[ok], o["count"][ok])
+
+
+def test_tune_cache_lines_without_the_last_field_still_apply(tmp_path):
+    """A cache line written before sparse_item_max existed (eleven fields) is applied with that
+    field at its default."""
+    wl = inputs.make("c1")
+    cache = str(tmp_path / "tune.txt")
+    s = B.Solver(wl.n, precision=FP32, tune_cache=cache)
+    s.sort(T(wl.pos), T(wl.mass))
+    best = s.autotune(T(wl.h0))
+    s.close()
+    line = open(cache).read().strip().splitlines()[-1].split()
+    assert len(line) == 12
+    old = " ".join(line[:1] + ["1", "2"] + line[3:11]) + "\n"  # group_shift 1, cell_div 2
+    open(cache, "w").write(old)
+    s2 = B.Solver(wl.n, precision=FP32, tune_cache=cache)
+    s2.set_tuning(sparse_item_max=4)
+    s2.sort(T(wl.pos), T(wl.mass))
+    t = s2.tuning()
+    s2.close()
+    assert (t["group_shift"], t["cell_div"], t["sparse_item_max"]) == (1, 2, 0)
+    assert best["sparse_item_max"] in (0, 1, 4)
+
+
 # ---- the paper's Wendland C6 kernel at 295 neighbours ------------------------------------------
 
 C6 = B.SPH_KERNEL_WENDLAND_C6
