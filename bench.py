@@ -877,9 +877,12 @@ def run_interact(args):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_gbs = BYTES_PER_INTERACT_PARTICLE * n / (t_max / 1e3) / 1e9
+    prof = profiled_interact_traffic()
     roof = {"bound": "alu", "kernel": "k_interact<FP32> (item set-up + staging + pair sums)",
             "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": None,
+            "traffic": prof["kernel_dram_bytes_per_launch"] * n / prof["capture_particles"] if prof else None,
+            "traffic_note": "DRAM bytes of one interaction kernel launch: ncu on the 8,388,608-particle set "
+                            "(profiles/interact_c5_8M.md), scaled by particle count",
             "peak_note": "measured: dependent-FMA probe (libsph_probe.so), timed alone with CUDA events",
             "peak_probe": probe, "flop_per_pair": FLOP_PER_INTERACT_PAIR, "pairs_per_step": pairs,
             "candidate_tests_per_step": sum(s_["pair_tests"] for s_ in st32) // max(1, len(st32)),
@@ -1087,6 +1090,26 @@ def profiled_replay_traffic():
         return {"capture_particles": int(get("capture_particles")),
                 "density_dram_bytes_per_step": get("density_dram_bytes_per_step"),
                 "step_dram_bytes_per_step": get("step_dram_bytes_per_step")}
+    except Exception:
+        return None
+
+
+def profiled_interact_traffic():
+    """DRAM bytes of one interaction kernel launch from the committed ncu summary (measured on
+    8.4M particles, to be scaled by particle count), while the kernel sources are the ones it was
+    captured from; else None."""
+    import hashlib
+    import re
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", "interact_c5_8M.md")).read()
+        src = b"".join(open(os.path.join(ROOT, "paper_1612_06090_gb300", "csrc", f), "rb").read()
+                       for f in ("sph_interact.cu", "sph_items.cuh", "sph_common.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] != re.search(r"kernel_source_sha256_16: (\w+)", text).group(1):
+            return None
+        get = lambda k: float(re.search(k + r": ([0-9.eE+]+)", text).group(1))  # noqa: E731
+        return {"capture_particles": int(get("capture_particles")),
+                "kernel_dram_bytes_per_launch": get("kernel_dram_bytes_per_launch")}
     except Exception:
         return None
 
