@@ -423,23 +423,16 @@ template <bool kF64, int kKern>
 cudaError_t launch_interact_t(const SolveArgs &a, const InteractArgs &ia, const int32_t *todo,
                               cudaStream_t st)
 {
-    static int blocks_per_sm = 0;  // per instantiation, asked once
-    const int smem = kIWarps * interact_warp_bytes<kF64>();
-    if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_interact<kF64, kKern>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_interact<kF64, kKern>, kIThreads, smem);
-        if (e != cudaSuccess) return e;
-        blocks_per_sm = b > 0 ? b : 1;
-    }
-    int dev = 0, sms = 0;
+    constexpr int smem = kIWarps * interact_warp_bytes<kF64>();
+    static_assert(smem <= 48 * 1024, "dynamic shared memory above 48 KB needs an opt-in per device");
+    // a persistent grid: as many blocks as are resident on the current device
+    int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interact<kF64, kKern>, kIThreads, smem);
     if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    k_interact<kF64, kKern><<<sms * blocks_per_sm, kIThreads, smem, st>>>(a, ia, todo);
+    k_interact<kF64, kKern><<<sms * (per_sm > 0 ? per_sm : 1), kIThreads, smem, st>>>(a, ia, todo);
     if (a.launches) *a.launches += 1;
     return cudaGetLastError();
 }
