@@ -180,6 +180,38 @@ def test_errors_and_recovery():
     s.close()
 
 
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_wendland_c6_clustered_against_oracle(precision):
+    # the paper's kernel at 295 neighbours on Plummer spheres + background
+    wl = inputs.make("c2", n=1 << 16, nngb=295.0, tol=5.0)
+    vel = inputs.velocities(wl.pos, 107, bulk=1.5, sigma=0.2)
+    h, g = gpu_interact(wl, vel, precision, B.SPH_KERNEL_WENDLAND_C6, 295.0)
+    o = oracle.interact(wl.pos, wl.mass, vel, h, box=wl.box, kernel="wendland_c6")
+    near = oracle.evaluate(wl.pos, wl.mass, h, box=wl.box, kernel="wendland_c6", near_rel=1e-6)["near"]
+    check(g, o, precision, near)
+
+
+def test_clumps_67M_sampled():
+    # full size: snapshot 0 of the 67M-particle clump set at its FP32-converged h, sampled targets
+    # against the oracle's brute force over every particle
+    wl = inputs.make("c5")
+    vel = inputs.velocities(wl.pos, 108)
+    s = B.Solver(wl.n, precision=FP32, box=wl.box, nngb=wl.nngb, tol=wl.tol, use_graph=True)
+    s.sort(T(wl.pos), T(wl.mass))
+    r = s.solve(T(wl.h0))
+    assert r["status"] == B.SPH_OK
+    out = s.interact(r["h"], T(vel))
+    torch.cuda.synchronize()
+    g = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    h = r["h"].cpu().numpy()
+    s.close()
+    rng = np.random.default_rng(67)
+    tg = np.sort(rng.choice(wl.n, size=32, replace=False))
+    o = oracle.interact(wl.pos, wl.mass, vel, h[tg], box=wl.box, targets=tg, mode="brute")
+    near = oracle.evaluate(wl.pos, wl.mass, h[tg], box=wl.box, targets=tg, mode="brute", near_rel=1e-6)["near"]
+    check(g, o, FP32, near, tg)
+
+
 def test_lognormal_16M_sampled():
     # full size: the 16.7M log-normal field (densities spanning orders of magnitude), FP32,
     # sampled targets against the oracle's brute force over every particle
