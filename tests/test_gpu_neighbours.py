@@ -174,3 +174,21 @@ def test_neighbour_export_argument_errors():
     torch.cuda.synchronize()
     assert np.all(cnt.cpu().numpy() == c.cpu().numpy()[:4])
     s.close()
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_neighbour_sets_lognormal_16M_at_converged_h(precision):
+    """Full size: the 16.7M-particle log-normal field at its FP32-converged h (densities over
+    orders of magnitude, the late passes' sparse targets included), sampled targets against the
+    brute-force sets over every particle."""
+    wl = inputs.make("c3")
+    s = B.Solver(wl.n, precision=FP32, box=wl.box, nngb=wl.nngb, tol=wl.tol, use_graph=True)
+    s.sort(T(wl.pos), T(wl.mass))
+    r = s.solve(T(wl.h0))
+    assert r["status"] == B.SPH_OK
+    h = r["h"].cpu().numpy()
+    s.close()
+    rng = np.random.default_rng(163)
+    sample = np.sort(rng.choice(wl.n, size=24, replace=False))
+    g = gpu_neighbours(wl.pos, wl.mass, h, sample, precision, box=wl.box)
+    compare_sets(g, wl.pos, h, sample, box=wl.box, exact=precision == FP64)
