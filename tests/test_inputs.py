@@ -66,3 +66,24 @@ def test_snapshot_series_matches_single_snapshots():
     for s in range(3):
         one = I.clumpy_snapshots(n=20000, n_clumps=8, snapshot=s)
         np.testing.assert_array_equal(series[s].pos, one.pos)
+
+
+def test_velocities_deterministic_periodic_and_scaled():
+    import numpy as np
+
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0, 1, (3, 5000))
+    a = inputs.velocities(pos, 11)
+    b = inputs.velocities(pos, 11)
+    np.testing.assert_array_equal(a, b)
+    assert a.shape == (3, 5000) and np.all(np.isfinite(a))
+    assert not np.array_equal(a, inputs.velocities(pos, 12))
+    # the smooth part is continuous across the periodic faces: with the random part off, a shift
+    # by one box length changes nothing (to rounding)
+    s0 = inputs.velocities(pos, 11, sigma=0.0)
+    s1 = inputs.velocities(pos + 1.0, 11, sigma=0.0)
+    np.testing.assert_allclose(s0, s1, rtol=0, atol=1e-9)
+    # rms of the smooth flow ~ bulk, of the random part ~ sigma
+    assert 0.3 < np.sqrt(np.mean(s0**2) * 3) < 3.0
+    r = inputs.velocities(pos, 11, bulk=0.0, sigma=0.3)
+    assert abs(np.std(r) - 0.3) < 0.02
